@@ -1,0 +1,234 @@
+"""Dense covariance matrices from point covariances (oracle; test infrastructure only).
+
+Measurement model: Hudgin-like two-point slopes (Appendix A.2).  The x-slope of
+the subaperture centred at c is the phase difference phi(c + d/2 x) - phi(c - d/2 x),
+the y-slope the same along y.  The lambda/(2 pi d) factor of the paper is
+dropped: slopes are phase differences in radians, which leaves the
+reconstructed phase unchanged (it cancels in Sigma_phi_s Sigma_ss^{-1}).
+
+Layered turbulence and the cone effect (Sec. 2 intro and Sec. 2.D, the
+paragraph on LGS sampling): the ray from guide star g (direction alpha_g,
+altitude H_g, H_g = 0 meaning a natural star at infinity) to pupil point p
+crosses layer k (altitude h_k) at  gamma_gk * p + h_k * alpha_g  with
+gamma_gk = 1 - h_k / H_g (1 for a natural star).  A target direction beta at
+infinity maps p to p + h_k * beta.  Layers are statistically independent, so
+
+    Sigma_ss[a, b] = sum_k sum_{u in a} sum_{v in b} w_u w_v B_k(|pos_k(u) - pos_k(v)|)
+
+with w = +1 / -1 for the two points of a slope, and likewise one phase point
+against one slope for Sigma_phi_s.  Entries are formed directly from these
+coordinates; nothing assumes the Toeplitz structure (Sec. 2.D) that the tests
+check for.
+
+Vector layout (Sec. 2.D, Eq. for Sigma_{s_i s_j}): guide stars in order, each
+as [x-slopes over valid subapertures ; y-slopes over valid subapertures],
+subapertures in row-major order.
+"""
+
+import math
+
+import numpy as np
+
+from . import geometry as geo
+from . import turbulence as turb
+
+
+def _gs(cfg):
+    return [(float(ax), float(ay), float(h)) for (ax, ay, h) in cfg["gs"]]
+
+
+def cone_factor(H, h):
+    """gamma = 1 - h/H for a laser star at altitude H, 1 for a natural star (H = 0)."""
+    return 1.0 if H == 0.0 else 1.0 - h / H
+
+
+def slope_points(cfg):
+    """Per-slope pupil points and weights.
+
+    Returns (pts, w, gsidx): pts (N, 2, 2) = [slope][point][x|y] in metres,
+    w (N, 2) = +1 / -1, gsidx (N,) = guide-star index of each slope.
+    """
+    n, D, eps = cfg["n"], cfg["D"], cfg["obstruction"]
+    d = D / n
+    c = geo.subaperture_centres(n, D, eps)
+    pts, w, gi = [], [], []
+    for g in range(len(cfg["gs"])):
+        for comp in (0, 1):
+            off = np.zeros(2)
+            off[comp] = d / 2.0
+            for cc in c:
+                pts.append([cc + off, cc - off])
+                w.append([1.0, -1.0])
+                gi.append(g)
+    return np.array(pts), np.array(w), np.array(gi, dtype=np.int64)
+
+
+def _layer_positions(cfg, pts, gsidx, k):
+    """Positions at layer k of the slope points: gamma * p + h_k * alpha."""
+    h, _ = cfg["layers"][k]
+    gs = _gs(cfg)
+    gam = np.array([cone_factor(gs[g][2], h) for g in gsidx])
+    alpha = np.array([[gs[g][0], gs[g][1]] for g in gsidx])
+    return gam[:, None, None] * pts + h * alpha[:, None, :]
+
+
+def css_rows(cfg, rows):
+    """Rows ``rows`` of the noiseless Sigma_ss (FP64), shape (len(rows), N)."""
+    pts, w, gsidx = slope_points(cfg)
+    rows = np.asarray(rows, dtype=np.int64)
+    out = np.zeros((len(rows), len(pts)))
+    for k, (h, frac) in enumerate(cfg["layers"]):
+        r0k = turb.layer_r0(cfg["r0"], frac)
+        pos = _layer_positions(cfg, pts, gsidx, k)
+        for u in (0, 1):
+            for v in (0, 1):
+                diff = pos[rows, u][:, None, :] - pos[None, :, v, :]
+                rho = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
+                out += (w[rows, u][:, None] * w[None, :, v]) * turb.vk_covariance(rho, r0k, cfg["L0"])
+    return out
+
+
+def css_dense(cfg, block=512):
+    """Full noiseless Sigma_ss (FP64), built in row blocks."""
+    N = slope_points(cfg)[0].shape[0]
+    out = np.empty((N, N))
+    for r0 in range(0, N, block):
+        rows = np.arange(r0, min(N, r0 + block))
+        out[rows] = css_rows(cfg, rows)
+    return out
+
+
+def noise_variance(cfg):
+    """Diagonal of Sigma_eta_eta: sigma_g^2 on every slope of guide star g (Sec. 2.B)."""
+    _, _, gsidx = slope_points(cfg)
+    sig = np.asarray(cfg["noise_sigma"], dtype=np.float64)
+    return sig[gsidx] ** 2
+
+
+def system_matrix(cfg):
+    """A = W_s (Sigma_ss + Sigma_eta_eta) W_s^T on valid slopes (Eq. SAap1)."""
+    A = css_dense(cfg)
+    A[np.diag_indices_from(A)] += noise_variance(cfg)
+    return A
+
+
+def cos_exact(cfg, target):
+    """Sigma_phi_beta_s on valid phase points x valid slopes (FP64), Eq. covIterative2.
+
+    Target phase point q at layer k sits at q + h_k * beta.
+    """
+    bx, by = cfg["targets"][target]
+    q = geo.phase_points(cfg["n"], cfg["D"], cfg["obstruction"])
+    pts, w, gsidx = slope_points(cfg)
+    out = np.zeros((len(q), len(pts)))
+    for k, (h, frac) in enumerate(cfg["layers"]):
+        r0k = turb.layer_r0(cfg["r0"], frac)
+        pos = _layer_positions(cfg, pts, gsidx, k)
+        qk = q + h * np.array([bx, by])
+        for v in (0, 1):
+            diff = qk[:, None, :] - pos[None, :, v, :]
+            rho = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
+            out += w[None, :, v] * turb.vk_covariance(rho, r0k, cfg["L0"])
+    return out
+
+
+def new_grid_size(cfg):
+    """n' of the common new phase grid (Sec. 2.D / 2.E, LGS Sigma_phi_s).
+
+    The grid of layer k has spacing d_k = gamma_k d and must cover the n + 1
+    target phase points spaced d, so n' >= n d / d_k + 1; one n' is shared by
+    all layers and set by the smallest gamma (highest layer).  For natural
+    stars gamma = 1 and n' = n + 1, the phase grid itself.
+    """
+    gs = _gs(cfg)
+    gmin = 1.0
+    for (_, _, H) in gs:
+        for (h, _) in cfg["layers"]:
+            gmin = min(gmin, cone_factor(H, h))
+    return int(math.ceil(cfg["n"] / gmin - 1e-9)) + 1
+
+
+def _common_cone(cfg, k):
+    """gamma_k shared by all guide stars (the interpolated form needs one altitude)."""
+    h = cfg["layers"][k][0]
+    gams = {cone_factor(H, h) for (_, _, H) in _gs(cfg)}
+    if len(gams) != 1:
+        raise ValueError("the new-grid Sigma_phi_s needs all guide stars at one altitude")
+    return gams.pop()
+
+
+def new_grid_nodes(cfg, k):
+    """Pupil coordinates of the n' x n' nodes of layer k, row-major, spacing gamma_k d,
+    centred on the pupil; node (uy, ux) sits at ((ux - (n'-1)/2) d_k, (uy - (n'-1)/2) d_k)."""
+    npr = new_grid_size(cfg)
+    dk = _common_cone(cfg, k) * cfg["D"] / cfg["n"]
+    u = (np.arange(npr) - (npr - 1) / 2.0) * dk
+    uy, ux = np.meshgrid(u, u, indexing="ij")
+    return np.stack([ux.ravel(), uy.ravel()], axis=1)
+
+
+def bilinear_weights(cfg, k):
+    """I'_k as a dense (n_vphi, n'^2) matrix of bilinear weights (Eq. interp)."""
+    npr = new_grid_size(cfg)
+    dk = _common_cone(cfg, k) * cfg["D"] / cfg["n"]
+    q = geo.phase_points(cfg["n"], cfg["D"], cfg["obstruction"])
+    I = np.zeros((len(q), npr * npr))
+    for a, (x, y) in enumerate(q):
+        tx = x / dk + (npr - 1) / 2.0
+        ty = y / dk + (npr - 1) / 2.0
+        ix = min(max(int(math.floor(tx)), 0), npr - 2)
+        iy = min(max(int(math.floor(ty)), 0), npr - 2)
+        fx, fy = tx - ix, ty - iy
+        I[a, iy * npr + ix] += (1 - fx) * (1 - fy)
+        I[a, iy * npr + ix + 1] += fx * (1 - fy)
+        I[a, (iy + 1) * npr + ix] += (1 - fx) * fy
+        I[a, (iy + 1) * npr + ix + 1] += fx * fy
+    return I
+
+
+def cos_new_grid_layer(cfg, target, k):
+    """Xi'_k: covariance of layer k's target phase on the new grid with all slopes."""
+    bx, by = cfg["targets"][target]
+    h, frac = cfg["layers"][k]
+    r0k = turb.layer_r0(cfg["r0"], frac)
+    nodes = new_grid_nodes(cfg, k) + h * np.array([bx, by])
+    pts, w, gsidx = slope_points(cfg)
+    pos = _layer_positions(cfg, pts, gsidx, k)
+    out = np.zeros((len(nodes), len(pts)))
+    for v in (0, 1):
+        diff = nodes[:, None, :] - pos[None, :, v, :]
+        rho = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
+        out += w[None, :, v] * turb.vk_covariance(rho, r0k, cfg["L0"])
+    return out
+
+
+def cos_interp(cfg, target):
+    """Sigma_phi_beta_s = sum_k I'_k Xi'_k (Sec. 2.D, Eq. interp and the sum over layers)."""
+    out = None
+    for k in range(len(cfg["layers"])):
+        term = bilinear_weights(cfg, k) @ cos_new_grid_layer(cfg, target, k)
+        out = term if out is None else out + term
+    return out
+
+
+def cos_interp_rows(cfg, target, rows):
+    """Rows ``rows`` (valid phase-point indices) of cos_interp, computing only the
+    grid nodes those rows interpolate from (same definition, restricted)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    npr = new_grid_size(cfg)
+    bx, by = cfg["targets"][target]
+    pts, w, gsidx = slope_points(cfg)
+    out = np.zeros((len(rows), len(pts)))
+    for k, (h, frac) in enumerate(cfg["layers"]):
+        I = bilinear_weights(cfg, k)[rows]
+        used = np.nonzero(np.abs(I).sum(axis=0))[0]
+        nodes = new_grid_nodes(cfg, k)[used] + h * np.array([bx, by])
+        r0k = turb.layer_r0(cfg["r0"], frac)
+        pos = _layer_positions(cfg, pts, gsidx, k)
+        X = np.zeros((len(used), len(pts)))
+        for v in (0, 1):
+            diff = nodes[:, None, :] - pos[None, :, v, :]
+            rho = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
+            X += w[None, :, v] * turb.vk_covariance(rho, r0k, cfg["L0"])
+        out += I[:, used] @ X
+    return out

@@ -1,0 +1,162 @@
+"""Seeded synthetic workloads: system configurations and slope frames.
+
+This module is the one place that serves both the CUDA path and the CPU
+oracle with inputs.  It holds no reconstructor arithmetic: it describes
+systems as plain numbers and simulates Shack-Hartmann measurements of
+synthetic von Karman phase screens (the paper measures on OOMAO simulations,
+which are not available; these frames stand in for them).
+
+Configurations (angles in radians, lengths in metres, r0 at 500 nm):
+
+* ``ngs8m``    -- 8 m pupil, no obstruction, 20 x 20 subapertures, 3 natural
+  guide stars on a 30" ring (0, 120, 240 deg), target on axis; layers
+  (0 km, 0.7), (8 km, 0.3); r0 = 0.15 m, L0 = 25 m; noise 5 % of slope rms.
+* ``elt_ltao`` -- 39 m pupil, 28 % obstruction, 74 x 74 subapertures, 6 laser
+  guide stars at 90 km on a 60"-diameter ring, target on axis; 9 layers from 0
+  to 20 km (a declared synthetic profile: the paper prints its profile only in
+  a figure); r0 = 0.129 m, L0 = 25 m; noise 3 % of slope rms.
+* ``lgs_mid``  -- the ``elt_ltao`` system shrunk to 16 x 16 subapertures of the
+  same size (8.43 m pupil), for tests the dense oracle finishes in seconds.
+
+Slope frames: per layer a periodic FFT phase screen with the von Karman PSD
+0.0228956 r0^{-5/3} (f^2 + 1/L0^2)^{-11/6} (Appendix A.1; the paper prints the
+constant rounded), pixel d/2, 512 pixels.  Rays from each guide star are traced
+to each layer with the cone factor 1 - h/H of laser stars; the x-slope of a
+subaperture is the trapezoid mean of the phase along its right edge minus that
+along its left edge (= d times the subaperture-averaged gradient), likewise in
+y.  Gaussian noise of standard deviation ``noise_frac`` times the rms of the
+noiseless slopes is added.  Every screen and noise draw comes from numpy's
+counter-based Philox generator keyed by (seed, frame, layer), so a frame does
+not depend on how many frames are generated with it.
+
+Slopes are returned on the full n x n subaperture grid,
+``[frame][gs][x|y][i][j]``; callers select the valid subapertures with the mask
+of the side they exercise.
+"""
+
+import math
+
+import numpy as np
+
+ARCSEC = math.pi / (180.0 * 3600.0)
+
+NINE_LAYER_H = [0.0, 500.0, 1000.0, 2000.0, 4000.0, 8000.0, 12000.0, 16000.0, 20000.0]
+NINE_LAYER_FRAC = [0.40, 0.12, 0.10, 0.09, 0.08, 0.07, 0.06, 0.05, 0.03]
+
+
+def ring(n_gs, radius, height, phase0=0.0):
+    """Guide stars evenly spaced on a ring, the first on +x: (ax, ay, H)."""
+    return [(radius * math.cos(phase0 + 2 * math.pi * j / n_gs),
+             radius * math.sin(phase0 + 2 * math.pi * j / n_gs), height) for j in range(n_gs)]
+
+
+def config(name):
+    """Plain-number system description (see module docstring)."""
+    if name == "ngs8m":
+        return dict(name=name, D=8.0, obstruction=0.0, n=20, r0=0.15, L0=25.0,
+                    layers=[(0.0, 0.7), (8000.0, 0.3)],
+                    gs=ring(3, 30 * ARCSEC, 0.0), targets=[(0.0, 0.0)], noise_frac=0.05)
+    if name == "elt_ltao":
+        return dict(name=name, D=39.0, obstruction=0.28, n=74, r0=0.129, L0=25.0,
+                    layers=list(zip(NINE_LAYER_H, NINE_LAYER_FRAC)),
+                    gs=ring(6, 30 * ARCSEC, 90e3), targets=[(0.0, 0.0)], noise_frac=0.03)
+    if name == "lgs_mid":
+        return dict(name=name, D=16 * 39.0 / 74, obstruction=0.28, n=16, r0=0.129, L0=25.0,
+                    layers=list(zip(NINE_LAYER_H, NINE_LAYER_FRAC)),
+                    gs=ring(6, 30 * ARCSEC, 90e3), targets=[(0.0, 0.0)], noise_frac=0.03)
+    raise KeyError(name)
+
+
+def _rng(seed, frame, stream):
+    return np.random.Generator(np.random.Philox(key=[seed, 1_000_003 * frame + stream]))
+
+
+def screen_pair(rng, N, pix, r0, L0):
+    """Two independent periodic von Karman screens (N x N, pixel ``pix``)."""
+    f = np.fft.fftfreq(N, d=pix)
+    fx, fy = np.meshgrid(f, f, indexing="xy")
+    psd = 0.0228956 * r0 ** (-5.0 / 3.0) * (fx * fx + fy * fy + 1.0 / L0 ** 2) ** (-11.0 / 6.0)
+    psd[0, 0] = 0.0
+    df = 1.0 / (N * pix)
+    amp = np.sqrt(psd) * df
+    z = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))) * amp
+    scr = np.fft.fft2(z)
+    return scr.real, scr.imag
+
+
+def bilinear(scr, pix, x, y):
+    N = scr.shape[0]
+    tx = x / pix + N / 2.0
+    ty = y / pix + N / 2.0
+    ix = np.floor(tx).astype(np.int64)
+    iy = np.floor(ty).astype(np.int64)
+    fx, fy = tx - ix, ty - iy
+    ix %= N
+    iy %= N
+    ix1, iy1 = (ix + 1) % N, (iy + 1) % N
+    return ((1 - fx) * (1 - fy) * scr[iy, ix] + fx * (1 - fy) * scr[iy, ix1]
+            + (1 - fx) * fy * scr[iy1, ix] + fx * fy * scr[iy1, ix1])
+
+
+def _clean_frame(cfg, seed, f, screen_px, grids):
+    """Noiseless slopes [gs][x|y][n][n] of frame ``f``."""
+    n, D = cfg["n"], cfg["D"]
+    pix = D / n / 2.0
+    (cx, cy), (vx, vy), (hx, hy) = grids
+    screens = []
+    rng = _rng(seed, f, 0)
+    for k in range(0, len(cfg["layers"]), 2):
+        pair = cfg["layers"][k:k + 2]
+        # one complex draw gives independent screens for layers k and k+1
+        a, b = screen_pair(rng, screen_px, pix, cfg["r0"], cfg["L0"])
+        for idx, (h, frac) in enumerate(pair):
+            screens.append((h, frac, a if idx == 0 else b))
+    out = np.zeros((len(cfg["gs"]), 2, n, n))
+    for g, (ax, ay, H) in enumerate(cfg["gs"]):
+        pc = np.zeros_like(cx)
+        pv = np.zeros_like(vx)
+        ph = np.zeros_like(hx)
+        for (h, frac, scr) in screens:
+            gam = 1.0 if H == 0.0 else 1.0 - h / H
+            s = math.sqrt(frac)                   # layer amplitude: r0_k^{-5/6} = frac^{1/2} r0^{-5/6}
+            pc += s * bilinear(scr, pix, gam * cx + h * ax, gam * cy + h * ay)
+            pv += s * bilinear(scr, pix, gam * vx + h * ax, gam * vy + h * ay)
+            ph += s * bilinear(scr, pix, gam * hx + h * ax, gam * hy + h * ay)
+        # edge means by the trapezoid rule over corner, midpoint, corner
+        right = (pc[:-1, 1:] + 2.0 * pv[:, 1:] + pc[1:, 1:]) / 4.0
+        left = (pc[:-1, :-1] + 2.0 * pv[:, :-1] + pc[1:, :-1]) / 4.0
+        top = (pc[1:, :-1] + 2.0 * ph[1:, :] + pc[1:, 1:]) / 4.0
+        bottom = (pc[:-1, :-1] + 2.0 * ph[:-1, :] + pc[:-1, 1:]) / 4.0
+        out[g, 0] = right - left
+        out[g, 1] = top - bottom
+    return out
+
+
+N_CALIBRATION_FRAMES = 4
+
+
+def slope_frames(cfg, n_frames, seed=0, screen_px=512):
+    """Noisy slopes [frame][gs][x|y][n][n] (float64) and the per-GS noise sigma.
+
+    Returns (slopes, noise_sigma): noise_sigma[g] = noise_frac * rms of the
+    noiseless slopes of guide star g over frames 0..3 of ``seed`` (always the
+    same frames, whatever ``n_frames`` is).
+    """
+    n, D = cfg["n"], cfg["D"]
+    d = D / n
+    e = (np.arange(n + 1) - n / 2.0) * d          # corner coordinates
+    m = (np.arange(n) + 0.5 - n / 2.0) * d        # centre coordinates
+    cy, cx = np.meshgrid(e, e, indexing="ij")     # (n+1, n+1) corners
+    vy, vx = np.meshgrid(m, e, indexing="ij")     # (n, n+1) midpoints of vertical edges
+    hy, hx = np.meshgrid(e, m, indexing="ij")     # (n+1, n) midpoints of horizontal edges
+    grids = ((cx, cy), (vx, vy), (hx, hy))
+    n_gs = len(cfg["gs"])
+    clean = [_clean_frame(cfg, seed, f, screen_px, grids)
+             for f in range(max(n_frames, N_CALIBRATION_FRAMES))]
+    calib = np.stack(clean[:N_CALIBRATION_FRAMES])
+    sigma = cfg["noise_frac"] * np.sqrt(np.mean(calib ** 2, axis=(0, 2, 3, 4)))
+    noisy = np.stack(clean[:n_frames])
+    for f in range(n_frames):
+        rng = _rng(seed, f, 999)
+        noisy[f] += sigma[:, None, None, None] * rng.standard_normal((n_gs, 2, n, n))
+    return noisy, sigma
