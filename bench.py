@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark: slope frames/s to relative residual 1e-4, ELT-scale LTAO, plain FP32 CG.
+
+Workload: 39 m pupil, 28 % obstruction, 74 x 74 subapertures, 6 laser guide
+stars at 90 km on a 60"-diameter ring, target on axis, 9 layers (0-20 km),
+r0 = 0.129 m, L0 = 25 m, noise 3 % of slope rms; 64 seeded synthetic frames per
+GPU per step.  One step = one call of tomo_solve on the 64 frames: CG with the
+FFT-based Sigma_ss MVM until every frame's FP64 true relative residual is
+<= 1e-4 (FP64 restarts included), then the Sigma_phi_s projection.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead (no GPU).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "slope frames/s to rel. residual 1e-4 (ELT LTAO), learned+mixed vs plain CG"
+UNIT = "frames/s"
+WORKLOAD = ("elt_ltao: 39 m, 28% obstruction, 6 LGS at 90 km (60\" ring), 74x74 subapertures, 9 layers 0-20 km, "
+            "r0 0.129 m, L0 25 m, noise 3%; plain FP32 CG (FP64 scalars, FP64 true residual) to 1e-4, then projection")
+FRAMES = 64
+TOL = 1e-4
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=FRAMES)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return dict(hbm_gbs=float(p["hbm_gbs"]), sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)), src="measured")
+    except (OSError, KeyError, ValueError):
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, src="fallback")
+
+
+# --------------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- algorithmic work model
+def fft_flops(L):
+    """Complex FFT of length L: 5 L log2 L flops (the paper's a = 5 cost model, Sec. 2.E and 4.B)."""
+    return 5.0 * L * math.log2(L)
+
+
+def kernel_model(layout):
+    """Algorithmic flops and bytes per frame-iteration for each MVM pass (roofline section)."""
+    n, P, NP, N = layout.n, layout.P, 2 * layout.n_gs, layout.N
+    nh = P // 2 + 1
+    rows_fft = NP * math.ceil(n / 2) * fft_flops(P)           # two real rows per complex FFT
+    inter = NP * nh * n * 8                                    # one pass of the column-major half spectrum
+    spectra = nh * P * NP * NP * 8                             # complex64 K(f), read once per launch
+    return {
+        "rows_fwd": dict(flops=rows_fft, bytes=3 * N * 4 + inter, per_launch_bytes=0),
+        "cols_mul": dict(flops=2 * NP * nh * fft_flops(P) + nh * P * NP * NP * 8, bytes=2 * inter,
+                         per_launch_bytes=spectra),
+        "rows_inv": dict(flops=rows_fft, bytes=2 * N * 4 + inter, per_launch_bytes=0),
+    }
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "fft.cuh", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1806_07938_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per frame-iteration of ``kernel`` from the committed ncu summary,
+    or None if the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    e = t.get("kernels", {}).get(kernel)
+    return None if e is None else e.get("dram_bytes_per_frame_iter")
+
+
+# --------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(cfg, frames=FRAMES):
+    """Times the oracle on a bounded sample of the workload and scales to frames/s.
+
+    The oracle's solve is the plain definition: assemble the dense FP64 matrix A
+    from point covariances, Cholesky-factor it once, and do two triangular solves
+    per frame.  Sample: R rows of A (assembly), a Cholesky of an n_s x n_s SPD
+    block and its triangular solves; times scale by N/R, (N/n_s)^3 and (N/n_s)^2.
+    """
+    import numpy as np
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+
+    from oracle import covariance as cov
+    from oracle import solve as osolve
+    cores = os.cpu_count() or 1
+    N = cov.slope_points(cfg)[0].shape[0]
+    R = 6 * cores
+    rows = np.linspace(0, N - 1, R).astype(np.int64)
+    chunks = [rows[i::cores] for i in range(cores)]
+    t0 = time.perf_counter()
+    with ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_rows_job, [(cfg, c) for c in chunks]))
+    t_rows = time.perf_counter() - t0
+    ns = 4096
+    rng = np.random.default_rng(0)
+    M = rng.standard_normal((ns, ns))
+    A = M @ M.T / ns + np.eye(ns)
+    b = rng.standard_normal((ns, frames))
+    t0 = time.perf_counter()
+    osolve.solve_cholesky(A, b[:, :1])                 # factor (+ one negligible solve)
+    t_chol = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    osolve.solve_cholesky(A, b)                        # factor + `frames` triangular-solve pairs
+    t_tri = max(time.perf_counter() - t0 - t_chol, 1e-6)
+    T_asm = t_rows * N / R
+    T_chol = t_chol * (N / ns) ** 3
+    T_tri = t_tri * (N / ns) ** 2
+    total = T_asm + T_chol + T_tri
+    return dict(value=frames / total, unit=UNIT, cores=cores, kind="oracle",
+                sample=(f"oracle dense FP64 path on {frames} frames, scaled from a bounded sample: assembly of {R} of "
+                        f"{N} rows of A from point covariances ({t_rows:.2f} s -> {T_asm:.0f} s), Cholesky of a "
+                        f"{ns}^2 SPD block ({t_chol:.2f} s -> {T_chol:.0f} s by (N/{ns})^3), triangular solves for "
+                        f"{frames} right-hand sides ({t_tri:.3f} s -> {T_tri:.1f} s by (N/{ns})^2)"))
+
+
+def _rows_job(args):
+    cfg, rows = args
+    from oracle import covariance as cov
+    return cov.css_rows(cfg, rows).shape
+
+
+# --------------------------------------------------------------------------- arms
+def dist_setup(use_cuda):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return world, rank, local, dist if world > 1 else None
+
+
+def workload(frames, seed):
+    from paper_1806_07938_gb300 import workloads as W
+    cfg = W.config("elt_ltao")
+    full, sigma = W.slope_frames(cfg, frames, seed=seed)
+    cfg["noise_sigma"] = [float(s) for s in sigma]
+    return cfg, full
+
+
+def run_reference(args):
+    world, rank, _, dist = dist_setup(False)
+    if rank != 0:
+        return
+    from paper_1806_07938_gb300 import workloads as W
+    cfg = W.config("elt_ltao")
+    cfg["noise_sigma"] = [0.17] * len(cfg["gs"])
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(cfg, frames=args.frames)
+        if i >= args.warmup:
+            vals.append(r)
+    value = statistics.median(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * args.frames / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames": args.frames},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[-1]["cores"], "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1806_07938_gb300 import tomo
+
+    world, rank, local, dist = dist_setup(True)
+    torch.cuda.set_device(local)
+    tomo.lib()
+    cfg, full = workload(args.frames, seed=1000 + rank)
+    stream = torch.cuda.Stream()
+    F = args.frames
+    with torch.cuda.stream(stream):
+        h = tomo.tomo_create(cfg, stream=stream, max_batch=F)
+        layout, sub, ph = tomo.tomo_layout(h)
+        s = torch.tensor(tomo.valid_slopes(full, sub), dtype=torch.float32, device="cuda").contiguous()
+        z = torch.zeros_like(s)
+        phi = torch.empty((F, layout.n_targets, layout.n_vphi), dtype=torch.float32, device="cuda")
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        opts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=32)
+        for _ in range(args.warmup):
+            tomo.tomo_solve(h, s, F, opts, z, phi)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        launches0 = tomo.tomo_launch_count(h)
+        clocks = Clocks(local)
+        clocks.start()
+        evs = []
+        t_wall = time.perf_counter()
+        infos = []
+        for _ in range(args.steps):
+            flush.zero_()                                   # L2 flush between timed steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(tomo.tomo_solve(h, s, F, opts, z, phi))
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        if dist:
+            dist.barrier()
+        clk = clocks.stop()
+        launches = tomo.tomo_launch_count(h) - launches0
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        total_ms = sum(step_ms)
+        if dist:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        value = world * F * args.steps / (total_ms / 1000.0)
+        info = infos[-1]
+        iters = info["iters"]
+        ok = bool((info["status"] == 0).all() and (info["relres"] <= TOL).all())
+
+        # one extra, separately reported step with per-kernel CUDA-event timing
+        tomo.tomo_set_kernel_timing(h, 1)
+        tomo.tomo_solve(h, s, F, opts, z, phi)
+        torch.cuda.synchronize()
+        kms, kn, frame_iters = tomo.tomo_get_kernel_timing(h)
+        tomo.tomo_set_kernel_timing(h, 0)
+        model = kernel_model(layout)
+        pk = peaks()
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
+        balance = alu_peak * 1e12 / (pk["hbm_gbs"] * 1e9)
+        dom = max(("rows_fwd", "cols_mul", "rows_inv"), key=lambda k: kms[k])
+        m = model[dom]
+        secs = kms[dom] / 1000.0
+        flops = m["flops"] * frame_iters
+        byts = m["bytes"] * frame_iters + m["per_launch_bytes"] * kn[dom]
+        if flops / byts > balance:
+            roof = {"bound": "alu", "achieved": flops / secs / 1e12, "peak": alu_peak, "unit": "TFLOP/s"}
+        else:
+            roof = {"bound": "hbm", "achieved": byts / secs / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        tr = ncu_traffic(dom)
+        roof["traffic"] = None if tr is None else tr * frame_iters / max(1, kn[dom])
+        roof["kernel"] = dom
+        roof["peak_source"] = ("FP32 FMA: %d SMs x %d lanes x 2 x %.0f MHz" % (SM_COUNT, FP32_LANES_PER_SM, pk["sm_max_mhz"])
+                               if roof["bound"] == "alu" else f"HBM copy, {pk['src']}")
+        roof["avg_launch_us"] = 1000.0 * kms[dom] / max(1, kn[dom])
+        roof["kernel_ms"] = {k: round(v, 3) for k, v in kms.items()}
+
+        # end to end through the public host-buffer API, inputs in pinned memory
+        s_h = torch.empty((F, layout.N), dtype=torch.float32, pin_memory=True)
+        s_h.copy_(s.cpu())
+        z_h = torch.empty((F, layout.N), dtype=torch.float32, pin_memory=True)
+        p_h = torch.empty((F, layout.n_targets, layout.n_vphi), dtype=torch.float32, pin_memory=True)
+        sn, zn, pn = s_h.numpy(), z_h.numpy(), p_h.numpy()
+        tomo.tomo_solve_host(h, sn, F, opts, zn, pn)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            tomo.tomo_solve_host(h, sn, F, opts, zn, pn)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * F * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": F * layout.N * 4,
+               "d2h_bytes_per_step": F * layout.N * 4 + F * layout.n_targets * layout.n_vphi * 4}
+        tomo.tomo_destroy(h)
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_gpu": F, "N": layout.N, "P": layout.P,
+                       "Pcos": layout.Pcos, "n_new": layout.n_new,
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
+                      "relres_max": float(info["relres"].max()), "all_converged": ok,
+                      "refinements_max": int(info["refinements"].max()),
+                      "step_ms": [round(x, 3) for x in step_ms], "wall_s": t_wall}}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(cfg, frames=F)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * tomo.h -- C ABI of the GB300 Toeplitz-structured spatio-angular MMSE
+ * tomographic wave-front reconstructor (Ono et al., "Fast iterative
+ * tomographic wave-front estimation with recursive Toeplitz reconstructor
+ * structure for large scale systems").
+ *
+ * The library solves, per slope frame s (Eq. covIterative1 with the aperture
+ * mask of Eq. SAap1),
+ *
+ *     W_s (Sigma_ss + Sigma_eta_eta) W_s^T zeta = s,
+ *
+ * by conjugate gradients whose every matrix-vector product applies Sigma_ss
+ * through its two-level recursive block-Toeplitz (2RBT) structure (Sec. 2.D,
+ * 2.E, Eq. mvm_ss): zero-pad -> 2-D FFT -> per-frequency (2 nGS) x (2 nGS)
+ * block multiply -> inverse 2-D FFT -> crop and mask.  It then projects to
+ * each target direction (Eq. covIterative2 / SAap2, Eqs. mvm_ps and
+ * ToeplitzLGS):  phi_hat = W_phi Sigma_phi_beta_s zeta.
+ *
+ * Measurement model: Hudgin-like two-point slopes (Appendix A.2); slopes are
+ * phase differences across a subaperture in radians at the wavelength of r0
+ * (the paper's lambda/(2 pi d) factor is dropped; it cancels in the
+ * reconstructor).  Turbulence: von Karman layers (Appendix A.2,
+ * structure-function equation).  Laser guide stars see layer k through the
+ * cone factor gamma = 1 - h_k / H (Sec. 2.D).
+ *
+ * Layouts (all row-major, C order):
+ *   slope / zeta vector of one frame: guide stars in order, each
+ *     [x-slopes over valid subapertures ; y-slopes over valid subapertures],
+ *     valid subapertures listed row-major, k(i, j) = i*n + j (Sec. 2.E);
+ *     N = 2 * n_gs * n_vs floats.  A batch is [batch][N].
+ *   phase of one frame: [target][valid phase point, row-major over (n+1)^2];
+ *     a batch is [batch][n_targets][n_vphi].
+ *   masks returned by tomo_layout: n*n and (n+1)*(n+1) bytes, 1 = valid.
+ *
+ * Ownership: the caller owns every buffer passed in; the handle owns its
+ * spectra, tables and workspaces.  Device-pointer entry points enqueue work on
+ * the handle's stream and return without synchronising; *_host entry points
+ * copy in, run and copy out, and return after the stream has finished.
+ *
+ * Errors: every call returns a tomo_status; on failure nothing is written to
+ * the outputs that the caller can rely on.  Per-frame non-convergence is not
+ * an error: it is reported in tomo_frame_info.status.
+ */
+#ifndef TOMO_H
+#define TOMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TOMO_OK = 0,
+    TOMO_EINVAL = 1,    /* bad argument or configuration                      */
+    TOMO_ENOMEM = 2,    /* device or host allocation failed                   */
+    TOMO_ECUDA = 3,     /* a CUDA runtime call failed                         */
+    TOMO_ETIMEOUT = 4,  /* a bounded device wait expired                      */
+    TOMO_ERANGE = 5     /* size beyond a compiled or configured maximum       */
+} tomo_status;
+
+/* Per-frame solver outcome (tomo_frame_info.status). */
+enum {
+    TOMO_FRAME_CONVERGED = 0,  /* FP64 true relative residual <= tol           */
+    TOMO_FRAME_MAXIT = 1,      /* iteration limit reached first                */
+    TOMO_FRAME_BREAKDOWN = 2   /* p^T A p <= 0 or not finite                   */
+};
+
+/* One guide star (Sec. 2 intro): direction alpha [rad] and altitude H [m];
+ * H = 0 denotes a natural guide star at infinity.  noise_sigma [rad] is the
+ * standard deviation of its slope noise: Sigma_eta_eta = sigma^2 I on its
+ * slopes (Sec. 2.B, diagonal noise covariance). */
+typedef struct {
+    double alpha_x, alpha_y;
+    double height;
+    double noise_sigma;
+} tomo_gs;
+
+/* System description.  Arrays are read during tomo_create only. */
+typedef struct {
+    double D;              /* pupil diameter [m]                                 */
+    double obstruction;    /* central obstruction, fraction of D (Sec. 2.F)       */
+    int n;                 /* subapertures across, the same for every WFS         */
+    int n_gs;              /* number of guide stars (>= 1)                        */
+    const tomo_gs* gs;     /* [n_gs]                                              */
+    int n_layers;          /* number of turbulent layers (>= 1)                   */
+    const double* layer_h;     /* [n_layers] altitudes [m]                        */
+    const double* layer_frac;  /* [n_layers] Cn^2 fractions, summing to 1         */
+    double r0;             /* Fried parameter [m] at the slope wavelength         */
+    double L0;             /* outer scale [m]                                     */
+    int n_targets;         /* target directions (>= 1)                            */
+    const double* target_x;    /* [n_targets] beta_x [rad]                        */
+    const double* target_y;    /* [n_targets] beta_y [rad]                        */
+    int fft_P;             /* padded FFT side for Sigma_ss, 0 = smallest valid    */
+    int fft_Pcos;          /* padded FFT side for Sigma_phi_s, 0 = smallest valid */
+    int max_batch;         /* frames per call the workspaces are sized for        */
+} tomo_config;
+
+typedef struct {
+    int n, n_gs, n_vs;     /* n_vs valid subapertures per WFS                     */
+    int N;                 /* unknowns per frame = 2 n_gs n_vs                    */
+    int n_vphi;            /* valid phase points                                  */
+    int n_targets, n_layers;
+    int P, Pcos;           /* padded FFT sides in use                             */
+    int n_new;             /* n' of the new phase grid of the projection          */
+    int max_batch;
+} tomo_layout_info;
+
+typedef struct {
+    double tol;            /* target FP64 true relative residual ||s-A z||/||s|| */
+    int max_iter;          /* CG iterations per call, over all refinement passes   */
+    int max_refine;        /* FP64 true-residual restarts after the first pass    */
+    int warm_start;        /* 1: zeta_dev holds the initial guess on entry        */
+    int check_every;       /* iterations between host convergence checks (>= 1)   */
+} tomo_solve_opts;
+
+typedef struct {
+    int iters;             /* CG iterations summed over refinement passes         */
+    int refinements;       /* restarts from the FP64 true residual                */
+    int status;            /* TOMO_FRAME_*                                        */
+    int pad_;
+    double relres;         /* FP64 true relative residual at exit                 */
+} tomo_frame_info;
+
+typedef struct tomo_handle tomo_handle;
+
+/* Builds geometry, the Sigma_ss and Sigma_phi_s generator vectors (FP64, on
+ * the device) and their spectra (Sec. 2.E: the FFT of the unique-element
+ * vector is computed once, offline).  cuda_stream may be NULL (legacy default
+ * stream).  Returns TOMO_EINVAL for an inconsistent configuration, e.g. a
+ * layer at or above a laser guide star, guide stars at different finite
+ * altitudes, fractions that are not positive, or an FFT side too small
+ * (P >= 2n - 1, Pcos >= n' + n - 1) or with a prime factor above 7. */
+tomo_status tomo_create(const tomo_config* cfg, void* cuda_stream, tomo_handle** out);
+
+/* Sizes and, if the pointers are non-NULL, host copies of the subaperture
+ * mask (n*n bytes) and phase-point mask ((n+1)*(n+1) bytes). */
+tomo_status tomo_layout(const tomo_handle* h, tomo_layout_info* info,
+                        uint8_t* subap_mask, uint8_t* phase_mask);
+
+/* y = W_s (Sigma_ss + Sigma_eta_eta) W_s^T x for `batch` frames, FP32 through
+ * the 2RBT MVM (Eq. mvm_ss plus the diagonal noise term of Eq. SAap1).
+ * x_dev, y_dev: device [batch][N] floats, must not alias. */
+tomo_status tomo_apply_css(tomo_handle* h, const float* x_dev, float* y_dev, int batch);
+
+/* The same operator with FP64 vectors, FFTs and spectra (used for the true
+ * residual of the solver). */
+tomo_status tomo_apply_css_f64(tomo_handle* h, const double* x_dev, double* y_dev, int batch);
+
+/* phi = W_phi Sigma_phi_beta_s W_s^T zeta for every target (Eq. SAap2), FP32.
+ * Natural guide stars: the exact 2RBT form (Eq. mvm_ps).  Laser guide stars:
+ * the per-layer new phase grid, bilinear interpolation and sum over layers
+ * (Eq. interp, Eq. ToeplitzLGS).  zeta_dev [batch][N], phase_dev
+ * [batch][n_targets][n_vphi] device floats. */
+tomo_status tomo_apply_cos(tomo_handle* h, const float* zeta_dev, float* phase_dev, int batch);
+
+/* Full reconstruction of `batch` frames: CG (FP32 vectors and MVMs, FP64
+ * dot products and alpha/beta) on Eq. SAap1, FP64 true residual at exit and
+ * restarts from it while it exceeds opts->tol, then the projection of
+ * Eq. SAap2.  slopes_dev [batch][N]; zeta_dev [batch][N] (warm start in if
+ * opts->warm_start); phase_dev [batch][n_targets][n_vphi] or NULL to skip the
+ * projection; info_host [batch] host memory or NULL.  opts NULL = defaults
+ * (tol 1e-4, max_iter 10000, max_refine 2, cold start, check_every 32).
+ * Synchronises the stream at each convergence check. */
+tomo_status tomo_solve(tomo_handle* h, const float* slopes_dev, int batch,
+                       const tomo_solve_opts* opts, float* zeta_dev, float* phase_dev,
+                       tomo_frame_info* info_host);
+
+/* tomo_solve on host buffers: copies slopes in and zeta / phase out around the
+ * solve (phase_host may be NULL).  Returns after the stream has finished. */
+tomo_status tomo_solve_host(tomo_handle* h, const float* slopes_host, int batch,
+                            const tomo_solve_opts* opts, float* zeta_host, float* phase_host,
+                            tomo_frame_info* info_host);
+
+/* Number of kernel launches the handle has issued since creation (a counter
+ * kept by the library, for launch accounting). */
+long long tomo_launch_count(const tomo_handle* h);
+
+/* Kernel timing.  With timing enabled, tomo_solve launches its CG iterations
+ * eagerly (no CUDA graph) with a CUDA event on the handle's stream before and
+ * after each MVM pass, and accumulates the elapsed times per pass:
+ *   [0] row-forward FFT pass, [1] column FFT + block-multiply pass,
+ *   [2] row-inverse FFT + mask pass, [3] CG vector update + scalars.
+ * Enabling or disabling resets the accumulators and the frame-iteration count
+ * (sum over frames of the CG iterations of the solves since the reset). */
+#define TOMO_NKERNELS 4
+tomo_status tomo_set_kernel_timing(tomo_handle* h, int enable);
+tomo_status tomo_get_kernel_timing(const tomo_handle* h, double* ms_total /*[TOMO_NKERNELS]*/,
+                                   long long* launches /*[TOMO_NKERNELS]*/, long long* frame_iters);
+
+void tomo_destroy(tomo_handle* h);
+
+const char* tomo_strerror(tomo_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOMO_H */

@@ -1,0 +1,745 @@
+// Host side of the C ABI declared in include/tomo.h.
+//
+// Index mapping of the 2RBT MVM (Sec. 2.E).  The paper writes y = T x for an
+// m^2 x n^2 two-level Toeplitz T as a 1-D FFT of length (m+n-1)^2 with the
+// shuffles S_1 (x reversed into the padded vector) and S_2 (read back).  Here
+// the same product is evaluated as the 2-D linear convolution
+//     y(a) = sum_b t(a - b) x(b),   a in [0,m)^2, b in [0,n)^2,
+// on a P x P periodic grid, P >= m + n - 1: x placed unreversed at its grid
+// position, the generator t stored at the wrapped lag (a - b) mod P, and y read
+// at a.  Both orderings give the same exact product (any P >= m + n - 1 avoids
+// wrap-around); the 2-D form lets the x-FFTs act on the n non-zero rows only
+// and lets the inverse keep only the m needed rows.
+//
+// Noise: Sigma_eta_eta = sigma_g^2 I per guide star (Sec. 2.B), applied as a
+// diagonal term after the masked gather (Eq. SAap1).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/tomo.h"
+#include "kernels.cuh"
+
+using namespace tomo;
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int B = -1, iters = 0;
+    long long nodes = 0;
+};
+
+struct tomo_handle {
+    // configuration
+    int n = 0, n_gs = 0, NP = 0, n_vs = 0, N = 0, n_vphi = 0, n_layers = 0, n_targets = 0;
+    int P = 0, Pc = 0, m = 0, cos_layers = 0, max_batch = 0;
+    double D = 0, obstruction = 0, d = 0, r0 = 0, L0 = 0;
+    bool all_ngs = true;
+    std::vector<double> tx, ty;
+    cudaStream_t stream = nullptr;     // the caller's stream
+    cudaStream_t work = nullptr;       // private stream of the solver (graph capture needs a non-legacy stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    long long launches = 0;
+    std::vector<uint8_t> subap_mask, phase_mask;
+    FftPlan plan{}, planc{};
+    MvmGeom g_ss{}, g_os{};
+    MaskTables mt{};
+    // device tables
+    int* d_rowstart = nullptr;
+    int* d_col = nullptr;
+    double* d_noise_var = nullptr;
+    float2* d_tw32 = nullptr;
+    double2* d_tw64 = nullptr;
+    float2* d_twc32 = nullptr;
+    float2* d_K32 = nullptr;
+    double2* d_K64 = nullptr;
+    float2* d_Kc32 = nullptr;
+    int* d_iidx = nullptr;
+    float* d_iw = nullptr;
+    // workspaces
+    float2 *X1 = nullptr, *Y1 = nullptr, *Xc = nullptr, *Yc = nullptr;
+    double2 *X1d = nullptr, *Y1d = nullptr;
+    float* Ydc = nullptr;
+    float *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
+    double *xd = nullptr, *yd = nullptr;
+    FrameState* st = nullptr;
+    double *pAp_part = nullptr, *rr_part = nullptr, *init_part = nullptr;
+    int nparts = 0;
+    int* d_nactive = nullptr;
+    int* h_nactive = nullptr;
+    float *s_stage = nullptr, *z_stage = nullptr, *phi_stage = nullptr;
+    GraphCache graph;
+    std::vector<void*> allocs;
+    // kernel timing (tomo_set_kernel_timing): eager CG iterations with events
+    bool timing = false;
+    double kt_ms[TOMO_NKERNELS] = {0};
+    long long kt_n[TOMO_NKERNELS] = {0};
+    long long frame_iters = 0;   // sum over frames of CG iterations in solves since the last reset
+    std::vector<cudaEvent_t> ev;
+};
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+#define CK(call)                                                         \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) {                                         \
+            std::fprintf(stderr, "tomo: %s failed: %s (%s:%d)\n", #call, \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);    \
+            return TOMO_ECUDA;                                           \
+        }                                                                \
+    } while (0)
+
+template <typename Tp>
+tomo_status dalloc(tomo_handle* h, Tp** ptr, size_t count) {
+    void* v = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&v, count * sizeof(Tp)) != cudaSuccess) {
+        cudaGetLastError();
+        return TOMO_ENOMEM;
+    }
+    h->allocs.push_back(v);
+    *ptr = static_cast<Tp*>(v);
+    return TOMO_OK;
+}
+
+#define TRY(expr)                          \
+    do {                                   \
+        tomo_status s_ = (expr);           \
+        if (s_ != TOMO_OK) return s_;      \
+    } while (0)
+
+// Radix plan for P (factors 2, 3, 4, 5, 7); false if P has another prime factor.
+bool make_plan(int P, FftPlan* pl) {
+    pl->P = P;
+    pl->nst = 0;
+    int r = P;
+    const int order[] = {5, 4, 3, 2, 7};
+    for (int rad : order) {
+        while (r % rad == 0) {
+            if (pl->nst >= 8) return false;
+            pl->rad[pl->nst++] = rad;
+            r /= rad;
+        }
+    }
+    return r == 1 && pl->nst > 0;
+}
+
+int smallest_fft_side(int pmin) {
+    for (int P = pmin + (pmin & 1); ; P += 2) {
+        FftPlan pl;
+        if (make_plan(P, &pl)) return P;
+    }
+}
+
+template <typename C>
+std::vector<C> twiddles(int P) {
+    std::vector<C> t(P);
+    for (int k = 0; k < P; ++k) {
+        const double a = -2.0 * kPi * (double)k / (double)P;
+        t[k].x = (decltype(t[k].x))std::cos(a);
+        t[k].y = (decltype(t[k].y))std::sin(a);
+    }
+    return t;
+}
+
+// Host-to-device copy ordered on the caller's stream (which may be non-blocking).
+tomo_status upload(tomo_handle* h, const void* host, void* dev, size_t bytes) {
+    CK(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return TOMO_OK;
+}
+
+Launch launch_of(tomo_handle* h) { return Launch{h->stream, &h->launches}; }
+
+// Sigma_ss + noise on FP32 or FP64 vectors.
+tomo_status apply_ss32(tomo_handle* h, const Launch& L, const float* x, float* y, int B, const FrameState* st,
+                       float* pgen, double* part) {
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, x, pgen, st, h->X1, h->d_tw32)));
+    CK((cols_mul<float>(L, h->g_ss, B, st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
+    // in CG mode the product is taken of the updated direction p
+    const float* xin = pgen ? pgen : x;
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, st, h->Y1, xin, h->d_noise_var, y, part, h->d_tw32)));
+    return TOMO_OK;
+}
+
+tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double* y, int B) {
+    CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1d, h->d_tw64)));
+    CK((cols_mul<double>(L, h->g_ss, B, nullptr, h->X1d, h->Y1d, h->d_K64, h->d_tw64)));
+    CK((rows_inv_masked<double, double>(L, h->g_ss, h->mt, B, nullptr, h->Y1d, x, h->d_noise_var, y, nullptr,
+                                        h->d_tw64)));
+    return TOMO_OK;
+}
+
+tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi, int B) {
+    CK((rows_fwd<float, float>(L, h->g_os, h->mt, B, z, nullptr, nullptr, h->Xc, h->d_twc32)));
+    const size_t kc_stride = (size_t)h->g_os.nh * h->Pc * h->cos_layers * h->NP;
+    for (int t = 0; t < h->n_targets; ++t) {
+        CK((cols_mul<float>(L, h->g_os, B, nullptr, h->Xc, h->Yc, h->d_Kc32 + t * kc_stride, h->d_twc32)));
+        CK((rows_inv_dense<float>(L, h->g_os, B, h->Yc, h->Ydc, h->d_twc32)));
+        CK(interp(L, B, h->n_targets, t, h->cos_layers, h->m, h->n_vphi, h->Ydc, h->d_iidx, h->d_iw, phi));
+    }
+    return TOMO_OK;
+}
+
+// One CG iteration on all active frames of the batch.
+tomo_status cg_iteration(tomo_handle* h, const Launch& L, int B) {
+    TRY(apply_ss32(h, L, h->r, h->Ap, B, h->st, h->p, h->pAp_part));
+    CK(cg_update(L, B, h->N, h->NP, h->nparts, h->p, h->Ap, h->x, h->r, h->pAp_part, h->rr_part, h->st));
+    CK(cg_scalars(L, B, h->NP, h->nparts, h->pAp_part, h->rr_part, 1 << 30, h->st));
+    return TOMO_OK;
+}
+
+// The same iteration launched eagerly with an event before and after each
+// kernel; the elapsed times are accumulated per kernel at the next sync.
+tomo_status cg_iteration_timed(tomo_handle* h, const Launch& L, int B, std::vector<std::pair<int, int>>& marks) {
+    auto mark = [&](void) -> int {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        h->ev.push_back(e);
+        cudaEventRecord(e, L.stream);
+        return (int)h->ev.size() - 1;
+    };
+    int e0 = mark();
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, h->r, h->p, h->st, h->X1, h->d_tw32)));
+    int e1 = mark();
+    CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
+    int e2 = mark();
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->Ap, h->pAp_part,
+                                      h->d_tw32)));
+    int e3 = mark();
+    CK(cg_update(L, B, h->N, h->NP, h->nparts, h->p, h->Ap, h->x, h->r, h->pAp_part, h->rr_part, h->st));
+    CK(cg_scalars(L, B, h->NP, h->nparts, h->pAp_part, h->rr_part, 1 << 30, h->st));
+    int e4 = mark();
+    if (e0 < 0 || e1 < 0 || e2 < 0 || e3 < 0 || e4 < 0) return TOMO_ECUDA;
+    marks.push_back({e0, e1});
+    marks.push_back({e1, e2});
+    marks.push_back({e2, e3});
+    marks.push_back({e3, e4});
+    return TOMO_OK;
+}
+
+void collect_timing(tomo_handle* h, std::vector<std::pair<int, int>>& marks) {
+    for (size_t i = 0; i < marks.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[marks[i].first], h->ev[marks[i].second]) == cudaSuccess) {
+            h->kt_ms[i % 4] += ms;
+            h->kt_n[i % 4] += 1;
+        }
+    }
+    marks.clear();
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+}
+
+tomo_status build_graph(tomo_handle* h, int B, int iters) {
+    if (h->graph.exec && h->graph.B == B && h->graph.iters == iters) return TOMO_OK;
+    if (h->graph.exec) {
+        cudaGraphExecDestroy(h->graph.exec);
+        h->graph.exec = nullptr;
+    }
+    long long before = h->launches;
+    CK(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
+    Launch Lc{h->work, &h->launches};
+    tomo_status s = TOMO_OK;
+    for (int i = 0; i < iters && s == TOMO_OK; ++i) s = cg_iteration(h, Lc, B);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->work, &graph);
+    const long long nodes = h->launches - before;
+    h->launches = before;
+    if (s != TOMO_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return TOMO_ECUDA;
+    e = cudaGraphInstantiate(&h->graph.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return TOMO_ECUDA;
+    h->graph.B = B;
+    h->graph.iters = iters;
+    h->graph.nodes = nodes;
+    return TOMO_OK;
+}
+
+tomo_status validate(const tomo_config* c) {
+    if (!c || !c->gs || !c->layer_h || !c->layer_frac || !c->target_x || !c->target_y) return TOMO_EINVAL;
+    if (c->n < 2 || c->n > 512 || c->n_gs < 1 || 2 * c->n_gs > 16 || c->n_layers < 1 || c->n_targets < 1)
+        return TOMO_EINVAL;
+    if (!(c->D > 0) || !(c->obstruction >= 0) || !(c->obstruction < 1) || !(c->r0 > 0) || !(c->L0 > 0))
+        return TOMO_EINVAL;
+    if (c->max_batch < 1 || c->max_batch > 4096) return TOMO_EINVAL;
+    const double H = c->gs[0].height;
+    for (int g = 0; g < c->n_gs; ++g) {
+        if (c->gs[g].height != H) return TOMO_EINVAL;  // one altitude: every Theta_pq block stays 2RBT
+        if (!(c->gs[g].height >= 0) || !(c->gs[g].noise_sigma >= 0)) return TOMO_EINVAL;
+    }
+    for (int k = 0; k < c->n_layers; ++k) {
+        if (!(c->layer_frac[k] > 0) || !(c->layer_h[k] >= 0)) return TOMO_EINVAL;
+        if (H > 0 && !(c->layer_h[k] < H)) return TOMO_EINVAL;
+    }
+    return TOMO_OK;
+}
+
+tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
+    h->stream = static_cast<cudaStream_t>(stream);
+    CK(init_kernel_attributes());
+    CK(cudaStreamCreateWithFlags(&h->work, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    h->n = c->n;
+    h->n_gs = c->n_gs;
+    h->NP = 2 * c->n_gs;
+    h->n_layers = c->n_layers;
+    h->n_targets = c->n_targets;
+    h->D = c->D;
+    h->obstruction = c->obstruction;
+    h->d = c->D / c->n;
+    h->r0 = c->r0;
+    h->L0 = c->L0;
+    h->max_batch = c->max_batch;
+    h->all_ngs = c->gs[0].height == 0.0;
+    const int n = h->n;
+
+    // --- geometry (Sec. 2.F): centre-in-annulus rule, in integers ---------------
+    h->subap_mask.assign((size_t)n * n, 0);
+    const double thr = (c->obstruction * n) * (c->obstruction * n);
+    std::vector<int> rowstart(n + 1, 0), col;
+    for (int i = 0; i < n; ++i) {
+        rowstart[i] = (int)col.size();
+        for (int j = 0; j < n; ++j) {
+            const long long a = 2LL * j + 1 - n, b = 2LL * i + 1 - n;
+            const long long q = a * a + b * b;
+            if (q <= (long long)n * n && (double)q >= thr) {
+                h->subap_mask[(size_t)i * n + j] = 1;
+                col.push_back(j);
+            }
+        }
+    }
+    rowstart[n] = (int)col.size();
+    h->n_vs = (int)col.size();
+    if (h->n_vs == 0) return TOMO_EINVAL;
+    h->N = h->NP * h->n_vs;
+    h->phase_mask.assign((size_t)(n + 1) * (n + 1), 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (h->subap_mask[(size_t)i * n + j])
+                for (int di = 0; di < 2; ++di)
+                    for (int dj = 0; dj < 2; ++dj) h->phase_mask[(size_t)(i + di) * (n + 1) + j + dj] = 1;
+    std::vector<int> pv_i, pv_j;
+    for (int i = 0; i <= n; ++i)
+        for (int j = 0; j <= n; ++j)
+            if (h->phase_mask[(size_t)i * (n + 1) + j]) { pv_i.push_back(i); pv_j.push_back(j); }
+    h->n_vphi = (int)pv_i.size();
+
+    // --- layers: B_k(0) = c_v (L0/r0)^{5/3} f_k and cone factors ------------------
+    const double cv = std::pow(24.0 / 5.0 * std::tgamma(6.0 / 5.0), 5.0 / 6.0) * std::tgamma(11.0 / 6.0) *
+                      std::tgamma(5.0 / 6.0) / (2.0 * std::pow(kPi, 8.0 / 3.0));
+    const double Hgs = c->gs[0].height;
+    std::vector<LayerGeom> layers(h->n_layers);
+    double gmin = 1.0;
+    for (int k = 0; k < h->n_layers; ++k) {
+        layers[k].h = c->layer_h[k];
+        layers[k].amp = cv * std::pow(c->L0 / c->r0, 5.0 / 3.0) * c->layer_frac[k];
+        layers[k].gamma = Hgs > 0 ? 1.0 - c->layer_h[k] / Hgs : 1.0;
+        gmin = std::min(gmin, layers[k].gamma);
+    }
+    // n' of the new phase grid (Sec. 2.D): covers the n+1 phase points at spacing gamma_min d
+    h->m = h->all_ngs ? n + 1 : (int)std::ceil((double)n / gmin - 1e-9) + 1;
+    h->cos_layers = h->all_ngs ? 1 : h->n_layers;
+
+    // --- FFT sides and plans ----------------------------------------------------------
+    h->P = c->fft_P > 0 ? c->fft_P : smallest_fft_side(2 * n - 1);
+    h->Pc = c->fft_Pcos > 0 ? c->fft_Pcos : smallest_fft_side(h->m + n - 1);
+    if (h->P < 2 * n - 1 || (h->P & 1) || h->Pc < h->m + n - 1 || (h->Pc & 1)) return TOMO_EINVAL;
+    if (!make_plan(h->P, &h->plan) || !make_plan(h->Pc, &h->planc)) return TOMO_EINVAL;
+    if (h->cos_layers > 16) return TOMO_ERANGE;
+    h->g_ss = MvmGeom{n, n, h->NP, h->NP, h->P / 2 + 1, h->plan};
+    h->g_os = MvmGeom{n, h->m, h->NP, h->cos_layers, h->Pc / 2 + 1, h->planc};
+
+    // --- device tables -------------------------------------------------------------
+    TRY(dalloc(h, &h->d_rowstart, n + 1));
+    TRY(dalloc(h, &h->d_col, h->n_vs));
+    TRY(upload(h, rowstart.data(), h->d_rowstart, sizeof(int) * (n + 1)));
+    TRY(upload(h, col.data(), h->d_col, sizeof(int) * h->n_vs));
+    h->mt = MaskTables{h->d_rowstart, h->d_col, h->n_vs};
+    std::vector<double> nvar(h->NP);
+    for (int p = 0; p < h->NP; ++p) nvar[p] = c->gs[p / 2].noise_sigma * c->gs[p / 2].noise_sigma;
+    TRY(dalloc(h, &h->d_noise_var, h->NP));
+    TRY(upload(h, nvar.data(), h->d_noise_var, sizeof(double) * h->NP));
+    auto tw32 = twiddles<float2>(h->P);
+    auto tw64 = twiddles<double2>(h->P);
+    auto twc32 = twiddles<float2>(h->Pc);
+    auto twc64 = twiddles<double2>(h->Pc);
+    double2* d_twc64 = nullptr;
+    TRY(dalloc(h, &h->d_tw32, h->P));
+    TRY(dalloc(h, &h->d_tw64, h->P));
+    TRY(dalloc(h, &h->d_twc32, h->Pc));
+    TRY(dalloc(h, &d_twc64, h->Pc));
+    TRY(upload(h, tw32.data(), h->d_tw32, sizeof(float2) * h->P));
+    TRY(upload(h, tw64.data(), h->d_tw64, sizeof(double2) * h->P));
+    TRY(upload(h, twc32.data(), h->d_twc32, sizeof(float2) * h->Pc));
+    TRY(upload(h, twc64.data(), d_twc64, sizeof(double2) * h->Pc));
+
+    // quadrature tables for K_{5/6} (step 0.2, t up to 40)
+    const int nq = 200;
+    const double hq = 0.2;
+    std::vector<double> ct(nq), cnt(nq);
+    for (int i = 0; i < nq; ++i) {
+        ct[i] = std::cosh(i * hq);
+        cnt[i] = std::cosh(5.0 / 6.0 * i * hq);
+    }
+    double *d_ct = nullptr, *d_cnt = nullptr, *d_alpha = nullptr;
+    LayerGeom* d_layers = nullptr;
+    TRY(dalloc(h, &d_ct, nq));
+    TRY(dalloc(h, &d_cnt, nq));
+    TRY(upload(h, ct.data(), d_ct, sizeof(double) * nq));
+    TRY(upload(h, cnt.data(), d_cnt, sizeof(double) * nq));
+    VkParams vk{c->L0, std::pow(2.0, 1.0 / 6.0) / std::tgamma(5.0 / 6.0), d_ct, d_cnt, nq, hq};
+    std::vector<double> alpha(2 * h->n_gs);
+    for (int g = 0; g < h->n_gs; ++g) { alpha[2 * g] = c->gs[g].alpha_x; alpha[2 * g + 1] = c->gs[g].alpha_y; }
+    TRY(dalloc(h, &d_alpha, 2 * h->n_gs));
+    TRY(upload(h, alpha.data(), d_alpha, sizeof(double) * 2 * h->n_gs));
+    TRY(dalloc(h, &d_layers, h->n_layers));
+    TRY(upload(h, layers.data(), d_layers, sizeof(LayerGeom) * h->n_layers));
+
+    Launch L = launch_of(h);
+    // --- Sigma_ss generators and spectra (FP64 on the device) ------------------------
+    {
+        const int npl = h->NP * h->NP;
+        const size_t Gsz = (size_t)npl * h->P * h->P;
+        double* G = nullptr;
+        double2* H = nullptr;
+        CK(cudaMalloc(&G, sizeof(double) * Gsz));
+        CK(cudaMalloc(&H, sizeof(double2) * (size_t)npl * (h->P / 2 + 1) * h->P));
+        TRY(dalloc(h, &h->d_K64, (size_t)npl * (h->P / 2 + 1) * h->P));
+        TRY(dalloc(h, &h->d_K32, (size_t)npl * (h->P / 2 + 1) * h->P));
+        CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
+        CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G));
+        CK(spectra(L, h->P, npl, h->NP, h->plan, G, H, h->d_tw64, h->d_K64, h->d_K32));
+        CK(cudaStreamSynchronize(h->stream));
+        cudaFree(G);
+        cudaFree(H);
+    }
+    // --- Sigma_phi_s generators and spectra, one set per target ------------------------
+    {
+        const int npl = h->cos_layers * h->NP;
+        const size_t Gsz = (size_t)npl * h->Pc * h->Pc;
+        const size_t kstride = (size_t)npl * (h->Pc / 2 + 1) * h->Pc;
+        double* G = nullptr;
+        double2* H = nullptr;
+        CK(cudaMalloc(&G, sizeof(double) * Gsz));
+        CK(cudaMalloc(&H, sizeof(double2) * (size_t)npl * (h->Pc / 2 + 1) * h->Pc));
+        TRY(dalloc(h, &h->d_Kc32, kstride * h->n_targets));
+        for (int t = 0; t < h->n_targets; ++t) {
+            CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
+            CK(gen_cos(L, n, h->m, h->Pc, h->NP, h->d, h->all_ngs ? -h->n_layers : h->n_layers, d_layers, d_alpha,
+                       c->target_x[t], c->target_y[t], vk, G));
+            CK(spectra(L, h->Pc, npl, h->NP, h->planc, G, H, d_twc64, nullptr, h->d_Kc32 + t * kstride));
+        }
+        CK(cudaStreamSynchronize(h->stream));
+        cudaFree(G);
+        cudaFree(H);
+    }
+    // --- bilinear interpolation I'_k (Eq. interp) from layer k's grid to the phase points ---
+    {
+        const int m = h->m, L_ = h->cos_layers;
+        std::vector<int> idx((size_t)L_ * h->n_vphi * 4);
+        std::vector<float> w((size_t)L_ * h->n_vphi * 4);
+        for (int k = 0; k < L_; ++k) {
+            const double dk = (h->all_ngs ? 1.0 : layers[k].gamma) * h->d;
+            for (int v = 0; v < h->n_vphi; ++v) {
+                const double x = (pv_j[v] - n / 2.0) * h->d, y = (pv_i[v] - n / 2.0) * h->d;
+                const double tx = x / dk + (m - 1) / 2.0, ty = y / dk + (m - 1) / 2.0;
+                const int ix = std::min(std::max((int)std::floor(tx), 0), m - 2);
+                const int iy = std::min(std::max((int)std::floor(ty), 0), m - 2);
+                const double fx = tx - ix, fy = ty - iy;
+                const size_t o = ((size_t)k * h->n_vphi + v) * 4;
+                idx[o + 0] = iy * m + ix;             w[o + 0] = (float)((1 - fx) * (1 - fy));
+                idx[o + 1] = iy * m + ix + 1;         w[o + 1] = (float)(fx * (1 - fy));
+                idx[o + 2] = (iy + 1) * m + ix;       w[o + 2] = (float)((1 - fx) * fy);
+                idx[o + 3] = (iy + 1) * m + ix + 1;   w[o + 3] = (float)(fx * fy);
+            }
+        }
+        TRY(dalloc(h, &h->d_iidx, idx.size()));
+        TRY(dalloc(h, &h->d_iw, w.size()));
+        TRY(upload(h, idx.data(), h->d_iidx, sizeof(int) * idx.size()));
+        TRY(upload(h, w.data(), h->d_iw, sizeof(float) * w.size()));
+    }
+
+    // --- workspaces --------------------------------------------------------------
+    const size_t B = h->max_batch;
+    const size_t nh = h->P / 2 + 1, nhc = h->Pc / 2 + 1;
+    TRY(dalloc(h, &h->X1, B * h->NP * nh * n));
+    TRY(dalloc(h, &h->Y1, B * h->NP * nh * n));
+    TRY(dalloc(h, &h->X1d, B * h->NP * nh * n));
+    TRY(dalloc(h, &h->Y1d, B * h->NP * nh * n));
+    TRY(dalloc(h, &h->Xc, B * h->NP * nhc * n));
+    TRY(dalloc(h, &h->Yc, B * h->cos_layers * nhc * h->m));
+    TRY(dalloc(h, &h->Ydc, B * h->cos_layers * h->m * h->m));
+    TRY(dalloc(h, &h->x, B * h->N));
+    TRY(dalloc(h, &h->r, B * h->N));
+    TRY(dalloc(h, &h->p, B * h->N));
+    TRY(dalloc(h, &h->Ap, B * h->N));
+    TRY(dalloc(h, &h->xd, B * h->N));
+    TRY(dalloc(h, &h->yd, B * h->N));
+    TRY(dalloc(h, &h->st, B));
+    h->nparts = std::max(1, std::min(64, (h->N + 4095) / 4096));
+    TRY(dalloc(h, &h->pAp_part, B * h->NP));
+    TRY(dalloc(h, &h->rr_part, B * h->nparts));
+    TRY(dalloc(h, &h->init_part, B * 2 * h->nparts));
+    TRY(dalloc(h, &h->d_nactive, 1));
+    TRY(dalloc(h, &h->s_stage, B * h->N));
+    TRY(dalloc(h, &h->z_stage, B * h->N));
+    TRY(dalloc(h, &h->phi_stage, B * h->n_targets * h->n_vphi));
+    CK(cudaMallocHost(&h->h_nactive, sizeof(int)));
+    CK(cudaStreamSynchronize(h->stream));
+    return TOMO_OK;
+}
+
+void release(tomo_handle* h) {
+    if (!h) return;
+    if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
+    if (h->work) cudaStreamSynchronize(h->work);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->work) cudaStreamDestroy(h->work);
+    if (h->h_nactive) cudaFreeHost(h->h_nactive);
+    delete h;
+}
+
+tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_opts& o, float* zeta, float* phase,
+                        tomo_frame_info* info) {
+    // the solve runs on the private stream, ordered after the caller's stream
+    // and before anything the caller enqueues next
+    Launch L{h->work, &h->launches};
+    CK(cudaEventRecord(h->ev_in, h->work));
+    CK(cudaStreamWaitEvent(h->work, h->ev_in, 0));
+    // the handle's x buffer holds zeta during the solve
+    if (o.warm_start) {
+        CK(cudaMemcpyAsync(h->x, zeta, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
+        TRY(apply_ss32(h, L, h->x, h->Ap, B, nullptr, nullptr, nullptr));
+        CK(cg_init(L, B, h->N, h->nparts, s, h->Ap, h->x, h->r, h->p, h->init_part));
+    } else {
+        CK(cg_init(L, B, h->N, h->nparts, s, nullptr, h->x, h->r, h->p, h->init_part));
+    }
+    CK(cg_init_scalars(L, B, h->nparts, h->init_part, o.tol, o.warm_start, h->st));
+    const int chunk = std::max(1, o.check_every);
+    if (!h->timing) TRY(build_graph(h, B, chunk));
+    long long total_iters = 0;
+    std::vector<std::pair<int, int>> marks;
+    for (;;) {
+        CK(count_active(L, B, h->st, h->d_nactive));
+        CK(cudaMemcpyAsync(h->h_nactive, h->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, h->work));
+        CK(cudaStreamSynchronize(h->work));
+        if (h->timing) collect_timing(h, marks);
+        if (*h->h_nactive == 0) {
+            // FP64 true residual s - A zeta and restart of the frames above tol
+            CK(to_f64(L, (size_t)B * h->N, h->x, h->xd));
+            TRY(apply_ss64(h, L, h->xd, h->yd, B));
+            CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->rr_part));
+            CK(true_residual_finalize(L, B, h->nparts, h->rr_part, o.tol, o.max_refine, h->st));
+            CK(count_active(L, B, h->st, h->d_nactive));
+            CK(cudaMemcpyAsync(h->h_nactive, h->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, h->work));
+            CK(cudaStreamSynchronize(h->work));
+            if (*h->h_nactive == 0) break;
+        }
+        if (total_iters >= (long long)o.max_iter) {
+            // iteration budget spent: stop the remaining frames
+            std::vector<FrameState> tmp(B);
+            CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
+            CK(cudaStreamSynchronize(h->work));
+            for (auto& f : tmp)
+                if (f.active) { f.active = 0; f.status = TOMO_FRAME_MAXIT; }
+            CK(cudaMemcpyAsync(h->st, tmp.data(), sizeof(FrameState) * B, cudaMemcpyHostToDevice, h->work));
+            CK(cudaStreamSynchronize(h->work));
+            CK(to_f64(L, (size_t)B * h->N, h->x, h->xd));
+            TRY(apply_ss64(h, L, h->xd, h->yd, B));
+            CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->rr_part));
+            CK(true_residual_finalize(L, B, h->nparts, h->rr_part, o.tol, 0, h->st));
+            break;
+        }
+        if (h->timing) {
+            for (int i = 0; i < chunk; ++i) TRY(cg_iteration_timed(h, L, B, marks));
+        } else {
+            CK(cudaGraphLaunch(h->graph.exec, h->work));
+            h->launches += h->graph.nodes;
+        }
+        total_iters += chunk;
+    }
+    CK(cudaMemcpyAsync(zeta, h->x, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
+    if (phase) TRY(apply_os(h, L, h->x, phase, B));
+    CK(cudaEventRecord(h->ev_out, h->work));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_out, 0));
+    if (info) {
+        std::vector<FrameState> tmp(B);
+        CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
+        CK(cudaStreamSynchronize(h->work));
+        for (int f = 0; f < B; ++f) {
+            h->frame_iters += tmp[f].iters;
+            info[f].iters = tmp[f].iters;
+            info[f].refinements = tmp[f].refinements;
+            info[f].status = tmp[f].status;
+            info[f].pad_ = 0;
+            info[f].relres = tmp[f].relres;
+        }
+    }
+    return TOMO_OK;
+}
+
+tomo_solve_opts default_opts() {
+    tomo_solve_opts o;
+    o.tol = 1e-4;
+    o.max_iter = 10000;
+    o.max_refine = 2;
+    o.warm_start = 0;
+    o.check_every = 32;
+    return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+tomo_status tomo_create(const tomo_config* cfg, void* cuda_stream, tomo_handle** out) {
+    if (!out) return TOMO_EINVAL;
+    *out = nullptr;
+    tomo_status s = validate(cfg);
+    if (s != TOMO_OK) return s;
+    tomo_handle* h = new (std::nothrow) tomo_handle();
+    if (!h) return TOMO_ENOMEM;
+    s = create_impl(cfg, cuda_stream, h);
+    if (s != TOMO_OK) {
+        cudaStreamSynchronize(h->stream);
+        release(h);
+        return s;
+    }
+    *out = h;
+    return TOMO_OK;
+}
+
+tomo_status tomo_layout(const tomo_handle* h, tomo_layout_info* info, uint8_t* subap_mask, uint8_t* phase_mask) {
+    if (!h || !info) return TOMO_EINVAL;
+    info->n = h->n;
+    info->n_gs = h->n_gs;
+    info->n_vs = h->n_vs;
+    info->N = h->N;
+    info->n_vphi = h->n_vphi;
+    info->n_targets = h->n_targets;
+    info->n_layers = h->n_layers;
+    info->P = h->P;
+    info->Pcos = h->Pc;
+    info->n_new = h->m;
+    info->max_batch = h->max_batch;
+    if (subap_mask) std::memcpy(subap_mask, h->subap_mask.data(), h->subap_mask.size());
+    if (phase_mask) std::memcpy(phase_mask, h->phase_mask.data(), h->phase_mask.size());
+    return TOMO_OK;
+}
+
+tomo_status tomo_apply_css(tomo_handle* h, const float* x, float* y, int batch) {
+    if (!h || !x || !y || batch < 0 || x == y) return TOMO_EINVAL;
+    Launch L = launch_of(h);
+    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        TRY(apply_ss32(h, L, x + (size_t)f0 * h->N, y + (size_t)f0 * h->N, B, nullptr, nullptr, nullptr));
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_apply_css_f64(tomo_handle* h, const double* x, double* y, int batch) {
+    if (!h || !x || !y || batch < 0 || x == y) return TOMO_EINVAL;
+    Launch L = launch_of(h);
+    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        TRY(apply_ss64(h, L, x + (size_t)f0 * h->N, y + (size_t)f0 * h->N, B));
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_apply_cos(tomo_handle* h, const float* z, float* phi, int batch) {
+    if (!h || !z || !phi || batch < 0) return TOMO_EINVAL;
+    Launch L = launch_of(h);
+    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        TRY(apply_os(h, L, z + (size_t)f0 * h->N, phi + (size_t)f0 * h->n_targets * h->n_vphi, B));
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_solve(tomo_handle* h, const float* slopes, int batch, const tomo_solve_opts* opts, float* zeta,
+                       float* phase, tomo_frame_info* info) {
+    if (!h || !slopes || !zeta || batch < 0) return TOMO_EINVAL;
+    tomo_solve_opts o = opts ? *opts : default_opts();
+    if (!(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 || o.check_every < 1) return TOMO_EINVAL;
+    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        TRY(solve_chunk(h, slopes + (size_t)f0 * h->N, B, o, zeta + (size_t)f0 * h->N,
+                        phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr, info ? info + f0 : nullptr));
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_solve_host(tomo_handle* h, const float* slopes, int batch, const tomo_solve_opts* opts, float* zeta,
+                            float* phase, tomo_frame_info* info) {
+    if (!h || !slopes || !zeta || batch < 0) return TOMO_EINVAL;
+    tomo_solve_opts o = opts ? *opts : default_opts();
+    const size_t nphi = (size_t)h->n_targets * h->n_vphi;
+    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        CK(cudaMemcpyAsync(h->s_stage, slopes + (size_t)f0 * h->N, sizeof(float) * B * h->N, cudaMemcpyHostToDevice,
+                           h->stream));
+        if (o.warm_start)
+            CK(cudaMemcpyAsync(h->z_stage, zeta + (size_t)f0 * h->N, sizeof(float) * B * h->N,
+                               cudaMemcpyHostToDevice, h->stream));
+        TRY(tomo_solve(h, h->s_stage, B, &o, h->z_stage, phase ? h->phi_stage : nullptr, info ? info + f0 : nullptr));
+        CK(cudaMemcpyAsync(zeta + (size_t)f0 * h->N, h->z_stage, sizeof(float) * B * h->N, cudaMemcpyDeviceToHost,
+                           h->stream));
+        if (phase)
+            CK(cudaMemcpyAsync(phase + (size_t)f0 * nphi, h->phi_stage, sizeof(float) * B * nphi,
+                               cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return TOMO_OK;
+}
+
+long long tomo_launch_count(const tomo_handle* h) { return h ? h->launches : 0; }
+
+tomo_status tomo_set_kernel_timing(tomo_handle* h, int enable) {
+    if (!h) return TOMO_EINVAL;
+    h->timing = enable != 0;
+    for (int k = 0; k < TOMO_NKERNELS; ++k) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
+    h->frame_iters = 0;
+    return TOMO_OK;
+}
+
+tomo_status tomo_get_kernel_timing(const tomo_handle* h, double* ms_total, long long* launches,
+                                   long long* frame_iters) {
+    if (!h || !ms_total || !launches) return TOMO_EINVAL;
+    for (int k = 0; k < TOMO_NKERNELS; ++k) { ms_total[k] = h->kt_ms[k]; launches[k] = h->kt_n[k]; }
+    if (frame_iters) *frame_iters = h->frame_iters;
+    return TOMO_OK;
+}
+
+void tomo_destroy(tomo_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+}
+
+const char* tomo_strerror(tomo_status s) {
+    switch (s) {
+        case TOMO_OK: return "ok";
+        case TOMO_EINVAL: return "invalid argument or configuration";
+        case TOMO_ENOMEM: return "out of memory";
+        case TOMO_ECUDA: return "CUDA runtime error";
+        case TOMO_ETIMEOUT: return "bounded device wait expired";
+        case TOMO_ERANGE: return "size beyond the supported maximum";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

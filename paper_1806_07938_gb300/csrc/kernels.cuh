@@ -1,0 +1,129 @@
+// Internal interface between the host side of the library (capi.cu) and the
+// device kernels (kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+
+namespace tomo {
+
+constexpr int kWarps = 8;              // warps per block in the FFT kernels
+constexpr int kThreads = 32 * kWarps;
+
+// Geometry of one FFT-based 2RBT product y = T x (Sec. 2.E): inputs are NPin
+// masked planes on an n x n grid, outputs NPout planes on an m x m grid, both
+// embedded in a P x P periodic grid (P >= m + n - 1); half spectrum nh = P/2+1.
+struct MvmGeom {
+    int n, m, NPin, NPout, nh;
+    FftPlan plan;
+};
+
+// Per-frame CG scalars (FP64), one per frame.
+struct FrameState {
+    double rr;       // r^T r of the current residual
+    double beta;     // beta applied by the next row-forward pass
+    double snorm2;   // ||s||^2
+    double tol2;     // (tol ||s||)^2
+    double relres;   // FP64 true relative residual (after a true-residual pass)
+    int iters;       // iterations done (all passes)
+    int active;      // 1 while CG runs on this frame
+    int status;      // TOMO_FRAME_*
+    int refinements; // restarts from the true residual
+};
+
+// Masked-vector index tables: valid entries of row r are [rowstart[r], rowstart[r+1]),
+// with column col[e]; the same tables serve input and output of Sigma_ss.
+struct MaskTables {
+    const int* rowstart;   // [n+1]
+    const int* col;        // [n_vs]
+    int n_vs;
+};
+
+struct Launch {
+    cudaStream_t stream;
+    long long* counter;    // incremented once per kernel launch
+};
+
+// Raises the dynamic shared-memory limit of every kernel to the device's
+// opt-in maximum (once per process and device, before any launch or capture).
+cudaError_t init_kernel_attributes();
+
+// --- MVM passes ---------------------------------------------------------
+// Row-forward pass: x [B][NPin][n_vs] (masked) -> X1T [B][NPin][nh][n].
+// With p != nullptr (CG mode) the pass first forms p = r + beta_f p on the fly,
+// writes it back to p, and transforms it; x is then r.
+template <typename T, typename TIn>
+cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B,
+                     const TIn* x, TIn* p, const FrameState* st,
+                     cplx_t<T>* X1T, const cplx_t<T>* tw);
+
+// Column pass: forward column FFT of the NPin planes, per-frequency block
+// multiply by K [nh][P][NPout][NPin], inverse column FFT, keep rows < m:
+// X1T [B][NPin][nh][n] -> Y1T [B][NPout][nh][m].
+template <typename T>
+cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState* st,
+                     const cplx_t<T>* X1T, cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw);
+
+// Row-inverse pass to masked output (Sigma_ss): y = crop/mask(IFFT rows) +
+// noise_var[plane] * xin; pAp partial dot per (frame, plane) if part != nullptr.
+template <typename T, typename TIn>
+cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B,
+                            const FrameState* st, const cplx_t<T>* Y1T, const TIn* xin,
+                            const double* noise_var, TIn* y, double* part, const cplx_t<T>* tw);
+
+// Row-inverse pass to a dense m x m output per plane: Yd [B][NPout][m][m].
+template <typename T>
+cudaError_t rows_inv_dense(const Launch& L, const MvmGeom& g, int B, const cplx_t<T>* Y1T,
+                           T* Yd, const cplx_t<T>* tw);
+
+// --- CG ---------------------------------------------------------------------
+cudaError_t cg_init(const Launch& L, int B, int N, int nparts, const float* s, const float* Ax0,
+                    float* x, float* r, float* p, double* parts);
+cudaError_t cg_init_scalars(const Launch& L, int B, int nparts, const double* parts, double tol,
+                            int warm, FrameState* st);
+cudaError_t cg_update(const Launch& L, int B, int N, int NP, int nparts, const float* p,
+                      const float* Ap, float* x, float* r, const double* pAp_part,
+                      double* rr_part, const FrameState* st);
+cudaError_t cg_scalars(const Launch& L, int B, int NP, int nparts, const double* pAp_part,
+                       const double* rr_part, int maxit, FrameState* st);
+cudaError_t to_f64(const Launch& L, size_t n, const float* a, double* b);
+cudaError_t true_residual(const Launch& L, int B, int N, int nparts, const float* s,
+                          const double* Ax, float* r, double* parts);
+cudaError_t true_residual_finalize(const Launch& L, int B, int nparts, const double* parts,
+                                   double tol, int max_refine, FrameState* st);
+cudaError_t count_active(const Launch& L, int B, const FrameState* st, int* n_active);
+
+// --- setup ------------------------------------------------------------------
+struct VkParams {
+    double L0;
+    double norm;     // 2^{1/6} / Gamma(5/6)
+    const double* cosh_t;    // quadrature table cosh(m h), m in [0, nq)
+    const double* cosh_nu_t; // cosh(5/6 m h)
+    int nq;
+    double h;
+};
+
+struct LayerGeom {
+    double h;        // altitude
+    double amp;      // c_v (L0/r0)^{5/3} f_k : B_k(0)
+    double gamma;    // cone factor shared by the guide stars
+};
+
+// Sigma_ss generators on the wrapped P x P grid: G[p*NP+q][P][P] (pre-zeroed).
+cudaError_t gen_css(const Launch& L, int n, int P, int NP, double d, int n_layers,
+                    const LayerGeom* layers, const double* gs_alpha, VkParams vk, double* G);
+// Sigma_phi_s generators of one target: G[k*NP+q][P][P] for the m x n 2RBT blocks.
+cudaError_t gen_cos(const Launch& L, int n, int m, int P, int NP, double d, int n_layers,
+                    const LayerGeom* layers, const double* gs_alpha, double bx, double by,
+                    VkParams vk, double* G);
+// Spectra: 2-D real FFT of each G plane, scaled by 1/P^2, into
+// K [nh][P][NPout][NPin] (plane index p*NPin + q), FP64 and FP32 copies.
+cudaError_t spectra(const Launch& L, int P, int npl, int NPin, const FftPlan& plan,
+                    const double* G, double2* H, const double2* tw64, double2* K64, float2* K32);
+// Bilinear interpolation of the projection: phi [B][T][n_vphi] (target t slot).
+cudaError_t interp(const Launch& L, int B, int T_all, int t, int n_layers, int m, int n_vphi,
+                   const float* Yd, const int* idx, const float* w, float* phi);
+
+}  // namespace tomo

@@ -1,0 +1,228 @@
+"""Thin ctypes binding of the C ABI in include/tomo.h (argument marshalling only).
+
+Every function here forwards to the function of the same name in
+``_lib/libtomo.so``; all arithmetic runs in that library's CUDA kernels.
+Device buffers are passed as torch CUDA tensors (their ``data_ptr()``), host
+buffers as numpy arrays.  There is no fallback: if the library is missing or a
+call fails, an exception is raised.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+TOMO_OK, TOMO_EINVAL, TOMO_ENOMEM, TOMO_ECUDA, TOMO_ETIMEOUT, TOMO_ERANGE = range(6)
+FRAME_CONVERGED, FRAME_MAXIT, FRAME_BREAKDOWN = range(3)
+
+
+class tomo_gs(ctypes.Structure):
+    _fields_ = [("alpha_x", ctypes.c_double), ("alpha_y", ctypes.c_double),
+                ("height", ctypes.c_double), ("noise_sigma", ctypes.c_double)]
+
+
+class tomo_config(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_double), ("obstruction", ctypes.c_double), ("n", ctypes.c_int),
+                ("n_gs", ctypes.c_int), ("gs", ctypes.POINTER(tomo_gs)),
+                ("n_layers", ctypes.c_int), ("layer_h", ctypes.POINTER(ctypes.c_double)),
+                ("layer_frac", ctypes.POINTER(ctypes.c_double)),
+                ("r0", ctypes.c_double), ("L0", ctypes.c_double),
+                ("n_targets", ctypes.c_int), ("target_x", ctypes.POINTER(ctypes.c_double)),
+                ("target_y", ctypes.POINTER(ctypes.c_double)),
+                ("fft_P", ctypes.c_int), ("fft_Pcos", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class tomo_layout_info(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in
+                ("n", "n_gs", "n_vs", "N", "n_vphi", "n_targets", "n_layers", "P", "Pcos", "n_new", "max_batch")]
+
+
+class tomo_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class tomo_frame_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refinements", ctypes.c_int), ("status", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("relres", ctypes.c_double)]
+
+
+FRAME_INFO_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("status", np.int32),
+                             ("pad_", np.int32), ("relres", np.float64)])
+
+EXPORTS = ("tomo_create", "tomo_layout", "tomo_apply_css", "tomo_apply_css_f64", "tomo_apply_cos",
+           "tomo_solve", "tomo_solve_host", "tomo_launch_count", "tomo_set_kernel_timing",
+           "tomo_get_kernel_timing", "tomo_destroy", "tomo_strerror")
+KERNEL_NAMES = ("rows_fwd", "cols_mul", "rows_inv", "cg_update")
+
+_lib = None
+
+
+class TomoError(RuntimeError):
+    def __init__(self, fn, status):
+        super().__init__(f"{fn} failed: {lib().tomo_strerror(status).decode()} (status {status})")
+        self.status = status
+
+
+def lib(path=None):
+    """Loads libtomo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with __graft_entry__.build() "
+                           "(or python -m paper_1806_07938_gb300._build)")
+    L = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.tomo_create.argtypes = [ctypes.POINTER(tomo_config), vp, ctypes.POINTER(vp)]
+    L.tomo_layout.argtypes = [vp, ctypes.POINTER(tomo_layout_info), vp, vp]
+    L.tomo_apply_css.argtypes = [vp, vp, vp, i]
+    L.tomo_apply_css_f64.argtypes = [vp, vp, vp, i]
+    L.tomo_apply_cos.argtypes = [vp, vp, vp, i]
+    L.tomo_solve.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
+    L.tomo_solve_host.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
+    L.tomo_launch_count.argtypes = [vp]
+    L.tomo_launch_count.restype = ctypes.c_longlong
+    L.tomo_set_kernel_timing.argtypes = [vp, i]
+    L.tomo_get_kernel_timing.argtypes = [vp, vp, vp, vp]
+    L.tomo_destroy.argtypes = [vp]
+    L.tomo_destroy.restype = None
+    L.tomo_strerror.argtypes = [i]
+    L.tomo_strerror.restype = ctypes.c_char_p
+    for fn in EXPORTS:
+        if fn not in ("tomo_launch_count", "tomo_destroy", "tomo_strerror"):
+            getattr(L, fn).restype = i
+    _lib = L
+    return L
+
+
+def _check(fn, status):
+    if status != TOMO_OK:
+        raise TomoError(fn, status)
+
+
+def _dptr(t, dtype):
+    """Device pointer of a contiguous CUDA tensor of the given torch dtype."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == dtype):
+        raise TypeError(f"expected a contiguous CUDA tensor of {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a, dtype):
+    if not (isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"] and a.dtype == dtype):
+        raise TypeError(f"expected a C-contiguous numpy array of {dtype}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0):
+    """tomo_config from the plain-number system description; keeps its arrays alive."""
+    n_gs = len(cfg["gs"])
+    gs = (tomo_gs * n_gs)()
+    for g, (ax, ay, H) in enumerate(cfg["gs"]):
+        gs[g] = tomo_gs(ax, ay, H, float(cfg["noise_sigma"][g]))
+    nl = len(cfg["layers"])
+    lh = (ctypes.c_double * nl)(*[h for h, _ in cfg["layers"]])
+    lf = (ctypes.c_double * nl)(*[f for _, f in cfg["layers"]])
+    nt = len(cfg["targets"])
+    tx = (ctypes.c_double * nt)(*[t[0] for t in cfg["targets"]])
+    ty = (ctypes.c_double * nt)(*[t[1] for t in cfg["targets"]])
+    c = tomo_config(cfg["D"], cfg["obstruction"], cfg["n"], n_gs, gs, nl, lh, lf, cfg["r0"], cfg["L0"],
+                    nt, tx, ty, fft_P, fft_Pcos, max_batch)
+    c._keep = (gs, lh, lf, tx, ty)
+    return c
+
+
+def tomo_create(cfg, stream=None, max_batch=1, fft_P=0, fft_Pcos=0):
+    """Creates a handle; ``stream`` is a torch.cuda.Stream or None (legacy default)."""
+    L = lib()
+    c = make_config(cfg, max_batch, fft_P, fft_Pcos)
+    h = ctypes.c_void_p()
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
+    _check("tomo_create", L.tomo_create(ctypes.byref(c), s, ctypes.byref(h)))
+    return h
+
+
+def tomo_layout(h):
+    info = tomo_layout_info()
+    _check("tomo_layout", lib().tomo_layout(h, ctypes.byref(info), None, None))
+    sub = np.zeros((info.n, info.n), np.uint8)
+    ph = np.zeros((info.n + 1, info.n + 1), np.uint8)
+    _check("tomo_layout", lib().tomo_layout(h, ctypes.byref(info), ctypes.c_void_p(sub.ctypes.data),
+                                            ctypes.c_void_p(ph.ctypes.data)))
+    return info, sub.astype(bool), ph.astype(bool)
+
+
+def tomo_apply_css(h, x, y, batch):
+    import torch
+    _check("tomo_apply_css", lib().tomo_apply_css(h, _dptr(x, torch.float32), _dptr(y, torch.float32), batch))
+
+
+def tomo_apply_css_f64(h, x, y, batch):
+    import torch
+    _check("tomo_apply_css_f64", lib().tomo_apply_css_f64(h, _dptr(x, torch.float64), _dptr(y, torch.float64), batch))
+
+
+def tomo_apply_cos(h, zeta, phase, batch):
+    import torch
+    _check("tomo_apply_cos", lib().tomo_apply_cos(h, _dptr(zeta, torch.float32), _dptr(phase, torch.float32), batch))
+
+
+def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=False, check_every=32):
+    return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every)
+
+
+def tomo_solve(h, slopes, batch, opts, zeta, phase=None):
+    """Device solve; returns the per-frame info as a numpy structured array."""
+    import torch
+    info = np.zeros(batch, FRAME_INFO_DTYPE)
+    _check("tomo_solve", lib().tomo_solve(
+        h, _dptr(slopes, torch.float32), batch, ctypes.byref(opts), _dptr(zeta, torch.float32),
+        _dptr(phase, torch.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)))
+    return info
+
+
+def tomo_solve_host(h, slopes, batch, opts, zeta, phase=None):
+    """Host-buffer solve (copies inside the call); returns the per-frame info."""
+    info = np.zeros(batch, FRAME_INFO_DTYPE)
+    _check("tomo_solve_host", lib().tomo_solve_host(
+        h, _hptr(slopes, np.float32), batch, ctypes.byref(opts), _hptr(zeta, np.float32),
+        _hptr(phase, np.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)))
+    return info
+
+
+def tomo_launch_count(h):
+    return lib().tomo_launch_count(h)
+
+
+def tomo_set_kernel_timing(h, enable):
+    _check("tomo_set_kernel_timing", lib().tomo_set_kernel_timing(h, int(bool(enable))))
+
+
+def tomo_get_kernel_timing(h):
+    """Returns ({kernel: total ms}, {kernel: launches}, frame_iterations)."""
+    ms = np.zeros(len(KERNEL_NAMES), np.float64)
+    n = np.zeros(len(KERNEL_NAMES), np.int64)
+    fi = ctypes.c_longlong(0)
+    _check("tomo_get_kernel_timing", lib().tomo_get_kernel_timing(
+        h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(n.ctypes.data), ctypes.byref(fi)))
+    return dict(zip(KERNEL_NAMES, ms.tolist())), dict(zip(KERNEL_NAMES, n.tolist())), fi.value
+
+
+def tomo_destroy(h):
+    if h:
+        lib().tomo_destroy(h)
+
+
+def tomo_strerror(status):
+    return lib().tomo_strerror(status).decode()
+
+
+def valid_slopes(full, mask):
+    """Selects the valid subapertures (row-major) from full-grid slopes [..., gs, 2, n, n]
+    into the ABI layout [..., N] (input marshalling; no arithmetic)."""
+    lead = full.shape[:-4]
+    return full[..., mask].reshape(*lead, -1)
