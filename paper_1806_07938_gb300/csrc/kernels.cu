@@ -120,6 +120,87 @@ cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, in
 // ---------------------------------------------------------------------------
 // Column pass with the per-frequency block multiply
 // ---------------------------------------------------------------------------
+// Per-frequency block product of Eq. mvm_ss for one column kx:
+//   y_p(ky) = sum_q K_pq(kx, ky) x_q(ky)   for every frame of the block,
+// in place in the column buffer D [frame][plane][ky].  K is stored
+// [kx][q][ky][p], so the threads of a round, one per (ky, p), read it fully
+// coalesced; each holds its row K_p.(ky) in registers and reads the x_q(ky)
+// as shared-memory broadcasts.  Results are held in registers until every
+// thread of the round has read its inputs.
+constexpr int kMaxFramesPerBlock = 8;
+
+template <typename C, int NPI, int NPO>
+__device__ __forceinline__ void block_mul(C* D, int NPmax, int P, int nf, const int* act, const C* __restrict__ Kc) {
+    using T = decltype(C::x);
+    const int kyr = blockDim.x / NPO;                 // ky values per round
+    const int kyl = threadIdx.x / NPO, pp = threadIdx.x % NPO;
+    for (int ky0 = 0; ky0 < P; ky0 += kyr) {
+        const int ky = ky0 + kyl;
+        const bool on = kyl < kyr && ky < P;
+        C k[NPI];
+        C y[kMaxFramesPerBlock];
+        if (on) {
+#pragma unroll
+            for (int q = 0; q < NPI; ++q) k[q] = __ldg(&Kc[((size_t)q * P + ky) * NPO + pp]);
+#pragma unroll
+            for (int fl = 0; fl < kMaxFramesPerBlock; ++fl) {
+                if (fl < nf && act[fl]) {
+                    const C* col = D + (size_t)fl * NPmax * P + ky;
+                    T ar = 0, ai = 0;
+#pragma unroll
+                    for (int q = 0; q < NPI; ++q) {
+                        const C x = col[q * P];
+                        ar = fma(k[q].x, x.x, ar);
+                        ar = fma(-k[q].y, x.y, ar);
+                        ai = fma(k[q].x, x.y, ai);
+                        ai = fma(k[q].y, x.x, ai);
+                    }
+                    y[fl] = cmk<C>(ar, ai);
+                }
+            }
+        }
+        __syncthreads();
+        if (on) {
+#pragma unroll
+            for (int fl = 0; fl < kMaxFramesPerBlock; ++fl)
+                if (fl < nf && act[fl]) D[((size_t)fl * NPmax + pp) * P + ky] = y[fl];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename C>
+__device__ void block_mul_rt(C* D, int NPmax, int P, int nf, const int* act, const C* __restrict__ Kc, int NPin,
+                             int NPout) {
+    using T = decltype(C::x);
+    const int kyr = blockDim.x / NPout;
+    const int kyl = threadIdx.x / NPout, pp = threadIdx.x % NPout;
+    for (int ky0 = 0; ky0 < P; ky0 += kyr) {
+        const int ky = ky0 + kyl;
+        const bool on = kyl < kyr && ky < P;
+        C y[kMaxFramesPerBlock];
+        if (on) {
+            for (int fl = 0; fl < nf; ++fl) {
+                if (!act[fl]) continue;
+                const C* col = D + (size_t)fl * NPmax * P + ky;
+                T ar = 0, ai = 0;
+                for (int q = 0; q < NPin; ++q) {
+                    const C kq = Kc[((size_t)q * P + ky) * NPout + pp];
+                    const C x = col[q * P];
+                    ar += kq.x * x.x - kq.y * x.y;
+                    ai += kq.x * x.y + kq.y * x.x;
+                }
+                y[fl] = cmk<C>(ar, ai);
+            }
+        }
+        __syncthreads();
+        if (on)
+            for (int fl = 0; fl < nf; ++fl)
+                if (act[fl]) D[((size_t)fl * NPmax + pp) * P + ky] = y[fl];
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __restrict__ X1T,
@@ -131,7 +212,7 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* scr = tw + P;
     C* D = scr + kWarps * P;                       // [Bc][NPmax][P]
-    __shared__ int act[64];
+    __shared__ int act[kMaxFramesPerBlock];
     const int kx = blockIdx.x;
     const int f0 = blockIdx.y * Bc;
     const int nf = min(Bc, B - f0);
@@ -153,24 +234,12 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     }
     __syncthreads();
     // block multiply: one thread per (ky, frame), frames fastest so K loads broadcast
-    const C* Kc = K + (size_t)kx * P * NPout * NPin;
-    for (int t = threadIdx.x; t < nf * P; t += blockDim.x) {
-        const int fl = t % nf, ky = t / nf;
-        if (!act[fl]) continue;
-        C xq[16];
-        for (int q = 0; q < NPin; ++q) xq[q] = D[((size_t)fl * NPmax + q) * P + ky];
-        const C* Kf = Kc + (size_t)ky * NPout * NPin;
-        for (int pp = 0; pp < NPout; ++pp) {
-            T ar = 0, ai = 0;
-            for (int q = 0; q < NPin; ++q) {
-                const C k = Kf[pp * NPin + q];
-                ar += k.x * xq[q].x - k.y * xq[q].y;
-                ai += k.x * xq[q].y + k.y * xq[q].x;
-            }
-            D[((size_t)fl * NPmax + pp) * P + ky] = cmk<C>(ar, ai);
-        }
-    }
-    __syncthreads();
+    const C* Kc = K + (size_t)kx * NPin * P * NPout;
+    if (NPin == 12 && NPout == 12) block_mul<C, 12, 12>(D, NPmax, P, nf, act, Kc);
+    else if (NPin == 6 && NPout == 6) block_mul<C, 6, 6>(D, NPmax, P, nf, act, Kc);
+    else if (NPin == 4 && NPout == 4) block_mul<C, 4, 4>(D, NPmax, P, nf, act, Kc);
+    else if (NPin == 2 && NPout == 2) block_mul<C, 2, 2>(D, NPmax, P, nf, act, Kc);
+    else block_mul_rt<C>(D, NPmax, P, nf, act, Kc, NPin, NPout);
     for (int t = warp; t < nf * NPout; t += kWarps) {
         const int fl = t / NPout, pp = t % NPout;
         if (act[fl]) fft_warp<C>(D + ((size_t)fl * NPmax + pp) * P, scr + warp * P, g.plan, tw, false, lane, 32);
@@ -193,7 +262,7 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
     const size_t budget = 72 * 1024;
     int Bc = (int)((budget > fixed ? budget - fixed : 0) / per_frame);
     if (Bc < 1) Bc = 1;
-    if (Bc > 64) Bc = 64;
+    if (Bc > kMaxFramesPerBlock) Bc = kMaxFramesPerBlock;
     if (Bc > B) Bc = B;
     const size_t smem = fixed + per_frame * Bc;
     auto kern = k_cols_mul<T>;
@@ -674,11 +743,13 @@ k_setup_rows(FftPlan plan, const double* __restrict__ G, double2* __restrict__ H
 __global__ void __launch_bounds__(kThreads)
 k_setup_cols(FftPlan plan, int NPin, int npl, const double2* __restrict__ H, const double2* __restrict__ twg,
              double2* __restrict__ K64, float2* __restrict__ K32) {
+    const int NPout = npl / NPin;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = plan.P, nh = P / 2 + 1;
     double2* tw = reinterpret_cast<double2*>(smem_raw);
     double2* wbuf = tw + P;
     const int pl = blockIdx.x;
+    const int pp = pl / NPin, q = pl % NPin;
     for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -689,7 +760,7 @@ k_setup_cols(FftPlan plan, int NPin, int npl, const double2* __restrict__ H, con
         __syncwarp();
         fft_warp<double2>(buf, buf + P, plan, tw, true, lane, 32);
         for (int ky = lane; ky < P; ky += 32) {
-            const size_t o = ((size_t)kx * P + ky) * npl + pl;
+            const size_t o = (((size_t)kx * NPin + q) * P + ky) * NPout + pp;
             const double2 v = make_double2(buf[ky].x * sc, buf[ky].y * sc);
             if (K64) K64[o] = v;
             if (K32) K32[o] = make_float2((float)v.x, (float)v.y);
@@ -698,7 +769,7 @@ k_setup_cols(FftPlan plan, int NPin, int npl, const double2* __restrict__ H, con
     }
 }
 
-cudaError_t spectra(const Launch& L, int P, int npl, int /*NPin*/, const FftPlan& plan, const double* G, double2* H,
+cudaError_t spectra(const Launch& L, int P, int npl, int NPin, const FftPlan& plan, const double* G, double2* H,
                     const double2* tw64, double2* K64, float2* K32) {
     const size_t smem = sizeof(double2) * (size_t)P * (1 + 2 * kWarps);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
@@ -706,7 +777,7 @@ cudaError_t spectra(const Launch& L, int P, int npl, int /*NPin*/, const FftPlan
     k_setup_rows<<<npl, kThreads, smem, L.stream>>>(plan, G, H, tw64);
     count(L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_setup_cols<<<npl, kThreads, smem, L.stream>>>(plan, 0, npl, H, tw64, K64, K32);
+    k_setup_cols<<<npl, kThreads, smem, L.stream>>>(plan, NPin, npl, H, tw64, K64, K32);
     count(L);
     return cudaGetLastError();
 }

@@ -60,7 +60,7 @@ cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, in
                      cplx_t<T>* X1T, const cplx_t<T>* tw);
 
 // Column pass: forward column FFT of the NPin planes, per-frequency block
-// multiply by K [nh][P][NPout][NPin], inverse column FFT, keep rows < m:
+// multiply by K [nh][NPin][P][NPout], inverse column FFT, keep rows < m:
 // X1T [B][NPin][nh][n] -> Y1T [B][NPout][nh][m].
 template <typename T>
 cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState* st,
@@ -119,7 +119,7 @@ cudaError_t gen_cos(const Launch& L, int n, int m, int P, int NP, double d, int 
                     const LayerGeom* layers, const double* gs_alpha, double bx, double by,
                     VkParams vk, double* G);
 // Spectra: 2-D real FFT of each G plane, scaled by 1/P^2, into
-// K [nh][P][NPout][NPin] (plane index p*NPin + q), FP64 and FP32 copies.
+// K [nh][NPin][P][NPout] (plane index p*NPin + q), FP64 and FP32 copies.
 cudaError_t spectra(const Launch& L, int P, int npl, int NPin, const FftPlan& plan,
                     const double* G, double2* H, const double2* tw64, double2* K64, float2* K32);
 // Bilinear interpolation of the projection: phi [B][T][n_vphi] (target t slot).
