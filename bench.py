@@ -119,10 +119,12 @@ def kernel_model(layout):
     inter = NP * nh * n * 8                                    # one pass of the column-major half spectrum
     spectra = nh * P * NP * NP * 8                             # complex64 K(f), read once per launch
     return {
-        "rows_fwd": dict(flops=rows_fft, bytes=3 * N * 4 + inter, per_launch_bytes=0),
+        # CG mode: reads x, r, p, Ap and writes x, r, p (the fused update), writes the half spectrum
+        "rows_fwd": dict(flops=rows_fft, bytes=7 * N * 4 + inter, per_launch_bytes=0),
         "cols_mul": dict(flops=2 * NP * nh * fft_flops(P) + nh * P * NP * NP * 8, bytes=2 * inter,
                          per_launch_bytes=spectra),
-        "rows_inv": dict(flops=rows_fft, bytes=2 * N * 4 + inter, per_launch_bytes=0),
+        # reads the half spectrum, p and r (for r^T Ap), writes Ap
+        "rows_inv": dict(flops=rows_fft, bytes=3 * N * 4 + inter, per_launch_bytes=0),
     }
 
 

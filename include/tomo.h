@@ -181,7 +181,7 @@ long long tomo_launch_count(const tomo_handle* h);
  * eagerly (no CUDA graph) with a CUDA event on the handle's stream before and
  * after each MVM pass, and accumulates the elapsed times per pass:
  *   [0] row-forward FFT pass, [1] column FFT + block-multiply pass,
- *   [2] row-inverse FFT + mask pass, [3] CG vector update + scalars.
+ *   [2] row-inverse FFT + mask pass, [3] per-frame CG scalars.
  * Enabling or disabling resets the accumulators and the frame-iteration count
  * (sum over frames of the CG iterations of the solves since the reset). */
 #define TOMO_NKERNELS 4

@@ -49,6 +49,7 @@ struct tomo_handle {
     // device tables
     int* d_rowstart = nullptr;
     int* d_col = nullptr;
+    int* d_rowcol = nullptr;
     double* d_noise_var = nullptr;
     float2* d_tw32 = nullptr;
     double2* d_tw64 = nullptr;
@@ -65,7 +66,7 @@ struct tomo_handle {
     float *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
     double *xd = nullptr, *yd = nullptr;
     FrameState* st = nullptr;
-    double *pAp_part = nullptr, *rr_part = nullptr, *init_part = nullptr;
+    double *dot_part = nullptr, *rr_part = nullptr, *init_part = nullptr, *res_part = nullptr;
     int nparts = 0;
     int* d_nactive = nullptr;
     int* h_nactive = nullptr;
@@ -156,16 +157,18 @@ tomo_status upload(tomo_handle* h, const void* host, void* dev, size_t bytes) {
 
 Launch launch_of(tomo_handle* h) { return Launch{h->stream, &h->launches}; }
 
-// Sigma_ss + noise on FP32 or FP64 vectors.
+// Sigma_ss + noise on FP32 vectors; with cg != nullptr, one CG product (see rows_fwd).
 tomo_status apply_ss32(tomo_handle* h, const Launch& L, const float* x, float* y, int B, const FrameState* st,
-                       float* pgen, double* part) {
-    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, x, pgen, st, h->X1, h->d_tw32)));
+                       const CgVecs* cg) {
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, x, cg, st, h->X1, h->d_tw32)));
     CK((cols_mul<float>(L, h->g_ss, B, st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
-    // in CG mode the product is taken of the updated direction p
-    const float* xin = pgen ? pgen : x;
-    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, st, h->Y1, xin, h->d_noise_var, y, part, h->d_tw32)));
+    const float* xin = cg ? cg->p : x;
+    float* yout = cg ? cg->Ap : y;
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, st, h->Y1, xin, h->d_noise_var, yout, cg, h->d_tw32)));
     return TOMO_OK;
 }
+
+CgVecs cg_vecs(tomo_handle* h) { return CgVecs{h->x, h->r, h->p, h->Ap, h->rr_part, h->dot_part}; }
 
 tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double* y, int B) {
     CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1d, h->d_tw64)));
@@ -186,11 +189,13 @@ tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi
     return TOMO_OK;
 }
 
-// One CG iteration on all active frames of the batch.
+// One CG iteration on all active frames of the batch: the previous update and
+// the new direction (row-forward pass), A p (column and row-inverse passes),
+// and the per-frame scalars.
 tomo_status cg_iteration(tomo_handle* h, const Launch& L, int B) {
-    TRY(apply_ss32(h, L, h->r, h->Ap, B, h->st, h->p, h->pAp_part));
-    CK(cg_update(L, B, h->N, h->NP, h->nparts, h->p, h->Ap, h->x, h->r, h->pAp_part, h->rr_part, h->st));
-    CK(cg_scalars(L, B, h->NP, h->nparts, h->pAp_part, h->rr_part, 1 << 30, h->st));
+    const CgVecs cg = cg_vecs(h);
+    TRY(apply_ss32(h, L, nullptr, nullptr, B, h->st, &cg));
+    CK(cg_scalars(L, B, h->NP, h->rr_part, h->dot_part, h->st));
     return TOMO_OK;
 }
 
@@ -204,16 +209,16 @@ tomo_status cg_iteration_timed(tomo_handle* h, const Launch& L, int B, std::vect
         cudaEventRecord(e, L.stream);
         return (int)h->ev.size() - 1;
     };
+    const CgVecs cg = cg_vecs(h);
     int e0 = mark();
-    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, h->r, h->p, h->st, h->X1, h->d_tw32)));
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32)));
     int e1 = mark();
     CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
     int e2 = mark();
-    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->Ap, h->pAp_part,
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->Ap, &cg,
                                       h->d_tw32)));
     int e3 = mark();
-    CK(cg_update(L, B, h->N, h->NP, h->nparts, h->p, h->Ap, h->x, h->r, h->pAp_part, h->rr_part, h->st));
-    CK(cg_scalars(L, B, h->NP, h->nparts, h->pAp_part, h->rr_part, 1 << 30, h->st));
+    CK(cg_scalars(L, B, h->NP, h->rr_part, h->dot_part, h->st));
     int e4 = mark();
     if (e0 < 0 || e1 < 0 || e2 < 0 || e3 < 0 || e4 < 0) return TOMO_ECUDA;
     marks.push_back({e0, e1});
@@ -267,7 +272,7 @@ tomo_status build_graph(tomo_handle* h, int B, int iters) {
 
 tomo_status validate(const tomo_config* c) {
     if (!c || !c->gs || !c->layer_h || !c->layer_frac || !c->target_x || !c->target_y) return TOMO_EINVAL;
-    if (c->n < 2 || c->n > 512 || c->n_gs < 1 || 2 * c->n_gs > 16 || c->n_layers < 1 || c->n_targets < 1)
+    if (c->n < 2 || c->n > 1024 || c->n_gs < 1 || 2 * c->n_gs > 16 || c->n_layers < 1 || c->n_targets < 1)
         return TOMO_EINVAL;
     if (!(c->D > 0) || !(c->obstruction >= 0) || !(c->obstruction < 1) || !(c->r0 > 0) || !(c->L0 > 0))
         return TOMO_EINVAL;
@@ -365,7 +370,12 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     TRY(dalloc(h, &h->d_col, h->n_vs));
     TRY(upload(h, rowstart.data(), h->d_rowstart, sizeof(int) * (n + 1)));
     TRY(upload(h, col.data(), h->d_col, sizeof(int) * h->n_vs));
-    h->mt = MaskTables{h->d_rowstart, h->d_col, h->n_vs};
+    std::vector<int> rowcol(h->n_vs);
+    for (int i = 0; i < n; ++i)
+        for (int e = rowstart[i]; e < rowstart[i + 1]; ++e) rowcol[e] = (i << 16) | col[e];
+    TRY(dalloc(h, &h->d_rowcol, h->n_vs));
+    TRY(upload(h, rowcol.data(), h->d_rowcol, sizeof(int) * h->n_vs));
+    h->mt = MaskTables{h->d_rowstart, h->d_col, h->d_rowcol, h->n_vs};
     std::vector<double> nvar(h->NP);
     for (int p = 0; p < h->NP; ++p) nvar[p] = c->gs[p / 2].noise_sigma * c->gs[p / 2].noise_sigma;
     TRY(dalloc(h, &h->d_noise_var, h->NP));
@@ -488,8 +498,9 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     TRY(dalloc(h, &h->yd, B * h->N));
     TRY(dalloc(h, &h->st, B));
     h->nparts = std::max(1, std::min(64, (h->N + 4095) / 4096));
-    TRY(dalloc(h, &h->pAp_part, B * h->NP));
-    TRY(dalloc(h, &h->rr_part, B * h->nparts));
+    TRY(dalloc(h, &h->dot_part, B * h->NP * 3));
+    TRY(dalloc(h, &h->rr_part, B * h->NP));
+    TRY(dalloc(h, &h->res_part, B * h->nparts));
     TRY(dalloc(h, &h->init_part, B * 2 * h->nparts));
     TRY(dalloc(h, &h->d_nactive, 1));
     TRY(dalloc(h, &h->s_stage, B * h->N));
@@ -522,10 +533,10 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
     // the handle's x buffer holds zeta during the solve
     if (o.warm_start) {
         CK(cudaMemcpyAsync(h->x, zeta, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
-        TRY(apply_ss32(h, L, h->x, h->Ap, B, nullptr, nullptr, nullptr));
-        CK(cg_init(L, B, h->N, h->nparts, s, h->Ap, h->x, h->r, h->p, h->init_part));
+        TRY(apply_ss32(h, L, h->x, h->Ap, B, nullptr, nullptr));
+        CK(cg_init(L, B, h->N, h->nparts, s, h->Ap, h->x, h->r, h->p, h->Ap, h->init_part));
     } else {
-        CK(cg_init(L, B, h->N, h->nparts, s, nullptr, h->x, h->r, h->p, h->init_part));
+        CK(cg_init(L, B, h->N, h->nparts, s, nullptr, h->x, h->r, h->p, h->Ap, h->init_part));
     }
     CK(cg_init_scalars(L, B, h->nparts, h->init_part, o.tol, o.warm_start, h->st));
     const int chunk = std::max(1, o.check_every);
@@ -541,8 +552,8 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             // FP64 true residual s - A zeta and restart of the frames above tol
             CK(to_f64(L, (size_t)B * h->N, h->x, h->xd));
             TRY(apply_ss64(h, L, h->xd, h->yd, B));
-            CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->rr_part));
-            CK(true_residual_finalize(L, B, h->nparts, h->rr_part, o.tol, o.max_refine, h->st));
+            CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->res_part));
+            CK(true_residual_finalize(L, B, h->nparts, h->res_part, o.tol, o.max_refine, h->st));
             CK(count_active(L, B, h->st, h->d_nactive));
             CK(cudaMemcpyAsync(h->h_nactive, h->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, h->work));
             CK(cudaStreamSynchronize(h->work));
@@ -559,8 +570,8 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             CK(cudaStreamSynchronize(h->work));
             CK(to_f64(L, (size_t)B * h->N, h->x, h->xd));
             TRY(apply_ss64(h, L, h->xd, h->yd, B));
-            CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->rr_part));
-            CK(true_residual_finalize(L, B, h->nparts, h->rr_part, o.tol, 0, h->st));
+            CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->res_part));
+            CK(true_residual_finalize(L, B, h->nparts, h->res_part, o.tol, 0, h->st));
             break;
         }
         if (h->timing) {
@@ -645,7 +656,7 @@ tomo_status tomo_apply_css(tomo_handle* h, const float* x, float* y, int batch) 
     Launch L = launch_of(h);
     for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
         const int B = std::min(h->max_batch, batch - f0);
-        TRY(apply_ss32(h, L, x + (size_t)f0 * h->N, y + (size_t)f0 * h->N, B, nullptr, nullptr, nullptr));
+        TRY(apply_ss32(h, L, x + (size_t)f0 * h->N, y + (size_t)f0 * h->N, B, nullptr, nullptr));
     }
     return TOMO_OK;
 }

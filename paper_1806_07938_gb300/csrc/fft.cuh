@@ -145,86 +145,11 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ in, C* __re
     }
 }
 
-// ---------------------------------------------------------------------------
-// Compile-time specialised transforms for the sizes the workloads use.  Same
-// Stockham ordering as above; P, Ns and R are constants, so the index
-// arithmetic folds and the butterfly loops unroll.  The twiddle index
-// r k P/(Ns R) is below P (k < Ns), so no modulo is needed.
-// ---------------------------------------------------------------------------
-template <typename C, int P, int Ns, int R, bool FWD>
-__device__ __forceinline__ void stage_ct(const C* __restrict__ in, C* __restrict__ out, const C* __restrict__ tw,
-                                         int lane) {
-    constexpr int PR = P / R;
-    constexpr int tstep = P / (Ns * R);
-#pragma unroll
-    for (int j0 = 0; j0 < PR; j0 += 32) {
-        const int j = j0 + lane;
-        if (j < PR) {
-            const int k = j % Ns;
-            C v[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = in[j + r * PR];
-            if (Ns > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    C w = tw[r * k * tstep];
-                    if (!FWD) w = cconj(w);
-                    v[r] = cmul(v[r], w);
-                }
-            }
-            SmallDft<C, R>::run(v, FWD);
-            const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
-        }
-    }
-}
-
-template <typename C, int P, int Ns, bool FWD, int... Rs> struct StagesCT;
-template <typename C, int P, int Ns, bool FWD> struct StagesCT<C, P, Ns, FWD> {
-    __device__ __forceinline__ static void run(C*, C*, const C*, int) {}
-};
-template <typename C, int P, int Ns, bool FWD, int R, int... Rest> struct StagesCT<C, P, Ns, FWD, R, Rest...> {
-    __device__ __forceinline__ static void run(C* src, C* dst, const C* tw, int lane) {
-        stage_ct<C, P, Ns, R, FWD>(src, dst, tw, lane);
-        __syncwarp();
-        StagesCT<C, P, Ns * R, FWD, Rest...>::run(dst, src, tw, lane);
-    }
-};
-
-template <typename C, int P, bool FWD, int... Rs>
-__device__ __forceinline__ void fft_ct(C* buf, C* scratch, const C* tw, int lane) {
-    StagesCT<C, P, 1, FWD, Rs...>::run(buf, scratch, tw, lane);
-    if (sizeof...(Rs) & 1) {       // odd number of stages: the result sits in scratch
-#pragma unroll
-        for (int j0 = 0; j0 < P; j0 += 32)
-            if (j0 + lane < P) buf[j0 + lane] = scratch[j0 + lane];
-        __syncwarp();
-    }
-}
-
-template <typename C, bool FWD>
-__device__ __forceinline__ bool fft_warp_special(C* buf, C* scratch, int P, const C* tw, int lane) {
-    switch (P) {
-        case 150: fft_ct<C, 150, FWD, 5, 5, 3, 2>(buf, scratch, tw, lane); return true;
-        case 180: fft_ct<C, 180, FWD, 5, 4, 3, 3>(buf, scratch, tw, lane); return true;
-        case 160: fft_ct<C, 160, FWD, 5, 4, 4, 2>(buf, scratch, tw, lane); return true;
-        case 40: fft_ct<C, 40, FWD, 5, 4, 2>(buf, scratch, tw, lane); return true;
-        case 32: fft_ct<C, 32, FWD, 4, 4, 2>(buf, scratch, tw, lane); return true;
-        default: return false;
-    }
-}
-
 // Transforms buf[0..P) in place (through scratch[0..P)) with the threads of one
 // warp (lane in [0, nl)).  Callers must __syncwarp() before (data written) and
 // may read buf after this returns (it ends with __syncwarp()).
 template <typename C>
 __device__ void fft_warp(C* buf, C* scratch, const FftPlan& pl, const C* tw, bool fwd, int lane, int nl) {
-    if (nl == 32) {
-        if (fwd ? fft_warp_special<C, true>(buf, scratch, pl.P, tw, lane)
-                : fft_warp_special<C, false>(buf, scratch, pl.P, tw, lane))
-            return;
-    }
     C* src = buf;
     C* dst = scratch;
     int Ns = 1;

@@ -18,6 +18,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "fft_group.cuh"
 #include "kernels.cuh"
 
 namespace tomo {
@@ -48,71 +49,104 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // ---------------------------------------------------------------------------
 // Row-forward pass
 // ---------------------------------------------------------------------------
-template <typename T, typename TIn>
-__global__ void __launch_bounds__(kThreads)
-k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, TIn* p, const FrameState* st,
+// Row pair (2j, 2j+1) of a plane is packed as one complex sequence
+// z = row_2j + i row_2j+1 in F[j][0..P); rows are padded to an odd stride so
+// that the column-wise accesses of the transposed write are conflict-free.
+__host__ __device__ constexpr int row_stride(int P) { return P | 1; }
+
+template <typename T, typename TIn, int PC>
+__global__ void __launch_bounds__(kThreads, TOMO_MIN_BLOCKS)
+k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const FrameState* st,
            cplx_t<T>* __restrict__ X1T, const cplx_t<T>* __restrict__ twg) {
     using C = cplx_t<T>;
+    constexpr int G = kFftGroup;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int P = g.plan.P, n = g.n, nh = g.nh;
+    __shared__ double red[kWarps];
+    const int P = g.plan.P, n = g.n, nh = g.nh, RS = row_stride(P);
+    const int npair = (n + 1) / 2;
+    const int ngrp = (npair + G - 1) / G;
     C* tw = reinterpret_cast<C*>(smem_raw);
-    C* wbuf = tw + P;
-    C* S = wbuf + kWarps * 2 * P;
+    C* scr = tw + P;                                // generic-path scratch, one per warp
+    C* F = scr + (Fused<PC>::ok ? 0 : kWarps * P);  // [ngrp * G][RS]
     const int q = blockIdx.x, f = blockIdx.y;
     if (st && !st[f].active) return;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t vbase = ((size_t)f * g.NPin + q) * mt.n_vs;
-    const TIn* xv = x + vbase;
-    TIn* pv = p ? p + vbase : nullptr;
-    const TIn beta = (p && st) ? (TIn)st[f].beta : (TIn)0;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
+    for (int i = threadIdx.x; i < ngrp * G * RS; i += blockDim.x) F[i] = cmk<C>(0, 0);
     __syncthreads();
-    C* buf = wbuf + warp * 2 * P;
-    C* scr = buf + P;
-    for (int r = 2 * warp; r < n; r += 2 * kWarps) {
-        for (int j = lane; j < P; j += 32) buf[j] = cmk<C>(0, 0);
-        __syncwarp();
-        for (int h = 0; h < 2 && r + h < n; ++h) {
-            const int e0 = mt.rowstart[r + h], e1 = mt.rowstart[r + h + 1];
-            for (int e = e0 + lane; e < e1; e += 32) {
-                T v;
-                if (pv) {
-                    const TIn pn = xv[e] + beta * pv[e];
-                    pv[e] = pn;
-                    v = (T)pn;
-                } else {
-                    v = (T)xv[e];
-                }
-                const int c = mt.col[e];
-                if (h == 0) buf[c].x = v; else buf[c].y = v;
+    // sweep over the plane's valid entries (W_s^T scatter), with the CG update
+    const size_t vbase = ((size_t)f * g.NPin + q) * mt.n_vs;
+    const bool cgm = cg.p != nullptr;
+    double rr = 0.0;
+    if (cgm) {
+        const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+            const size_t i = vbase + e;
+            const int rc = mt.rowcol[e];
+            const float pe = cg.p[i];
+            float re = cg.r[i];
+            if (alpha != 0.f) {
+                const float ape = cg.Ap[i];
+                cg.x[i] += alpha * pe;
+                re -= alpha * ape;
+                cg.r[i] = re;
             }
+            const float pn = re + beta * pe;
+            cg.p[i] = pn;
+            rr += (double)re * re;
+            const int row = rc >> 16, col = rc & 0xffff;
+            T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
+            *dst = (T)pn;
         }
-        __syncwarp();
-        fft_warp<C>(buf, scr, g.plan, tw, true, lane, 32);
-        // two real spectra from one complex one: A = (Z_k + conj Z_{P-k})/2, B = (Z_k - conj Z_{P-k})/(2i)
-        for (int k = lane; k < nh; k += 32) {
-            const C zk = buf[k];
-            const C zc = cconj(buf[k == 0 ? 0 : P - k]);
-            const C a = cscale(cadd(zk, zc), (T)0.5);
-            const C dd = csub(zk, zc);
-            S[k * n + r] = a;
-            if (r + 1 < n) S[k * n + r + 1] = cmk<C>((T)0.5 * dd.y, (T)-0.5 * dd.x);
+    } else {
+#pragma unroll 4
+        for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+            const int rc = mt.rowcol[e];
+            const int row = rc >> 16, col = rc & 0xffff;
+            T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
+            *dst = (T)x[vbase + e];
         }
-        __syncwarp();
     }
     __syncthreads();
+    for (int gi = warp; gi < ngrp; gi += kWarps) fft_g<PC, C, true>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane);
+    if (cgm) {
+        const double t = block_sum<T>(rr, red);
+        if (threadIdx.x == 0) cg.rr_part[(size_t)f * g.NPin + q] = t;
+    }
+    __syncthreads();
+    // unpack the two real spectra of each pair, A = (Z_k + conj Z_{P-k})/2,
+    // B = (Z_k - conj Z_{P-k})/(2i), and write them column-major [kx][row]
     C* out = X1T + ((size_t)f * g.NPin + q) * nh * n;
-    for (int i = threadIdx.x; i < nh * n; i += blockDim.x) out[i] = S[i];
+    for (int k = warp; k < nh; k += kWarps) {
+        const int kc = k == 0 ? 0 : P - k;
+        for (int j = lane; j < npair; j += 32) {
+            const C zk = F[j * RS + k];
+            const C zc = cconj(F[j * RS + kc]);
+            const C dd = csub(zk, zc);
+            out[(size_t)k * n + 2 * j] = cscale(cadd(zk, zc), (T)0.5);
+            if (2 * j + 1 < n) out[(size_t)k * n + 2 * j + 1] = cmk<C>((T)0.5 * dd.y, (T)-0.5 * dd.x);
+        }
+    }
+}
+
+template <typename T>
+size_t rows_smem(const MvmGeom& g, int nrows) {
+    const int G = kFftGroup;
+    const int npair = (nrows + 1) / 2, ngrp = (npair + G - 1) / G;
+    const int scratch = has_fused_plan(g.plan.P) ? 0 : kWarps;
+    return sizeof(cplx_t<T>) * ((size_t)g.plan.P * (1 + scratch) + (size_t)ngrp * G * row_stride(g.plan.P));
 }
 
 template <typename T, typename TIn>
-cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const TIn* x, TIn* p,
+cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const TIn* x, const CgVecs* cg,
                      const FrameState* st, cplx_t<T>* X1T, const cplx_t<T>* tw) {
-    using C = cplx_t<T>;
-    const size_t smem = sizeof(C) * ((size_t)g.plan.P * (1 + 2 * kWarps) + (size_t)g.nh * g.n);
-    auto kern = k_rows_fwd<T, TIn>;
+    const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const size_t smem = rows_smem<T>(g, g.n);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
-    kern<<<dim3(g.NPin, B), kThreads, smem, L.stream>>>(g, mt, x, p, st, X1T, tw);
+#define TOMO_L(PC) k_rows_fwd<T, TIn, PC><<<dim3(g.NPin, B), kThreads, smem, L.stream>>>(g, mt, x, cgv, st, X1T, tw)
+    TOMO_DISPATCH_P(g.plan.P, TOMO_L)
+#undef TOMO_L
     count(L);
     return cudaGetLastError();
 }
@@ -201,17 +235,19 @@ __device__ void block_mul_rt(C* D, int NPmax, int P, int nf, const int* act, con
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, int PC>
+__global__ void __launch_bounds__(kThreads, TOMO_MIN_BLOCKS)
 k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __restrict__ X1T,
            cplx_t<T>* __restrict__ Y1T, const cplx_t<T>* __restrict__ K, const cplx_t<T>* __restrict__ twg) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = g.plan.P, n = g.n, m = g.m, nh = g.nh, NPin = g.NPin, NPout = g.NPout;
-    const int NPmax = NPin > NPout ? NPin : NPout;
+    constexpr int G = kFftGroup;
+    int NPmax = NPin > NPout ? NPin : NPout;
+    NPmax += NPmax & 1;                            // even: groups of two planes never cross frames
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* scr = tw + P;
-    C* D = scr + kWarps * P;                       // [Bc][NPmax][P]
+    C* D = scr + (Fused<PC>::ok ? 0 : kWarps * P); // [Bc][NPmax][P]
     __shared__ int act[kMaxFramesPerBlock];
     const int kx = blockIdx.x;
     const int f0 = blockIdx.y * Bc;
@@ -228,21 +264,31 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
         D[((size_t)fl * NPmax + q) * P + r] = v;
     }
     __syncthreads();
-    for (int t = warp; t < nf * NPin; t += kWarps) {
-        const int fl = t / NPin, q = t % NPin;
-        if (act[fl]) fft_warp<C>(D + ((size_t)fl * NPmax + q) * P, scr + warp * P, g.plan, tw, true, lane, 32);
+    {
+        const int gpf = NPin / G;                  // NPin is even
+        for (int t = warp; t < nf * gpf; t += kWarps) {
+            const int fl = t / gpf, q0 = (t % gpf) * G;
+            if (!act[fl]) continue;
+            C* base = D + ((size_t)fl * NPmax + q0) * P;
+            fft_g<PC, C, true>(base, P, G, g.plan, tw, scr + warp * P, lane);
+        }
     }
     __syncthreads();
-    // block multiply: one thread per (ky, frame), frames fastest so K loads broadcast
+    // block multiply: one thread per (ky, p), frames looped
     const C* Kc = K + (size_t)kx * NPin * P * NPout;
     if (NPin == 12 && NPout == 12) block_mul<C, 12, 12>(D, NPmax, P, nf, act, Kc);
     else if (NPin == 6 && NPout == 6) block_mul<C, 6, 6>(D, NPmax, P, nf, act, Kc);
     else if (NPin == 4 && NPout == 4) block_mul<C, 4, 4>(D, NPmax, P, nf, act, Kc);
     else if (NPin == 2 && NPout == 2) block_mul<C, 2, 2>(D, NPmax, P, nf, act, Kc);
     else block_mul_rt<C>(D, NPmax, P, nf, act, Kc, NPin, NPout);
-    for (int t = warp; t < nf * NPout; t += kWarps) {
-        const int fl = t / NPout, pp = t % NPout;
-        if (act[fl]) fft_warp<C>(D + ((size_t)fl * NPmax + pp) * P, scr + warp * P, g.plan, tw, false, lane, 32);
+    {
+        const int gpf = (NPout + G - 1) / G;       // the last group may include the pad plane
+        for (int t = warp; t < nf * gpf; t += kWarps) {
+            const int fl = t / gpf, p0 = (t % gpf) * G;
+            if (!act[fl]) continue;
+            C* base = D + ((size_t)fl * NPmax + p0) * P;
+            fft_g<PC, C, false>(base, P, NPout - p0, g.plan, tw, scr + warp * P, lane);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nf * NPout * m; i += blockDim.x) {
@@ -256,8 +302,9 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
                      cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw) {
     using C = cplx_t<T>;
     if (g.NPin > 16) return cudaErrorInvalidValue;
-    const int NPmax = g.NPin > g.NPout ? g.NPin : g.NPout;
-    const size_t fixed = sizeof(C) * (size_t)g.plan.P * (1 + kWarps);
+    int NPmax = g.NPin > g.NPout ? g.NPin : g.NPout;
+    NPmax += NPmax & 1;
+    const size_t fixed = sizeof(C) * (size_t)g.plan.P * (1 + (has_fused_plan(g.plan.P) ? 0 : kWarps));
     const size_t per_frame = sizeof(C) * (size_t)NPmax * g.plan.P;
     const size_t budget = 72 * 1024;
     int Bc = (int)((budget > fixed ? budget - fixed : 0) / per_frame);
@@ -265,9 +312,11 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
     if (Bc > kMaxFramesPerBlock) Bc = kMaxFramesPerBlock;
     if (Bc > B) Bc = B;
     const size_t smem = fixed + per_frame * Bc;
-    auto kern = k_cols_mul<T>;
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
-    kern<<<dim3(g.nh, (B + Bc - 1) / Bc), kThreads, smem, L.stream>>>(g, B, Bc, st, X1T, Y1T, K, tw);
+#define TOMO_L(PC) \
+    k_cols_mul<T, PC><<<dim3(g.nh, (B + Bc - 1) / Bc), kThreads, smem, L.stream>>>(g, B, Bc, st, X1T, Y1T, K, tw)
+    TOMO_DISPATCH_P(g.plan.P, TOMO_L)
+#undef TOMO_L
     count(L);
     return cudaGetLastError();
 }
@@ -291,88 +340,133 @@ __device__ __forceinline__ void pack_row_pair(const C* S, int m, int r, int P, i
     }
 }
 
-template <typename T, typename TIn>
-__global__ void __launch_bounds__(kThreads)
-k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T>* __restrict__ Y1T,
-                  const TIn* __restrict__ xin, const double* __restrict__ noise_var, TIn* __restrict__ y,
-                  double* part, const cplx_t<T>* __restrict__ twg) {
-    using C = cplx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[kWarps];
-    const int P = g.plan.P, m = g.m, nh = g.nh;
-    C* tw = reinterpret_cast<C*>(smem_raw);
-    C* wbuf = tw + P;
-    C* S = wbuf + kWarps * 2 * P;
-    const int pp = blockIdx.x, f = blockIdx.y;
-    if (st && !st[f].active) return;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
-    const C* src = Y1T + ((size_t)f * g.NPout + pp) * nh * m;
-    for (int i = threadIdx.x; i < nh * m; i += blockDim.x) S[i] = src[i];
-    __syncthreads();
+// Loads the half spectra [kx][row] of the m kept rows of one plane into F as
+// packed row pairs z_k = A_k + i B_k over the full k range (Hermitian
+// extension; DC and Nyquist taken real), so that one inverse complex FFT per
+// pair returns row 2j in .x and row 2j+1 in .y.
+template <typename C>
+__device__ __forceinline__ void load_row_pairs(const C* __restrict__ src, int m, int P, int nh, int RS, C* F) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C* buf = wbuf + warp * 2 * P;
-    const size_t vbase = ((size_t)f * g.NPout + pp) * mt.n_vs;
-    const TIn nv = (TIn)noise_var[pp];
-    double acc = 0.0;
-    for (int r = 2 * warp; r < m; r += 2 * kWarps) {
-        pack_row_pair<C>(S, m, r, P, nh, buf, lane);
-        __syncwarp();
-        fft_warp<C>(buf, buf + P, g.plan, tw, false, lane, 32);
-        for (int h = 0; h < 2 && r + h < m; ++h) {
-            const int e0 = mt.rowstart[r + h], e1 = mt.rowstart[r + h + 1];
-            for (int e = e0 + lane; e < e1; e += 32) {
-                const C z = buf[mt.col[e]];
-                const TIn xi = xin[vbase + e];
-                const TIn out = (TIn)(h == 0 ? z.x : z.y) + nv * xi;
-                y[vbase + e] = out;
-                acc += (double)xi * (double)out;
+    const int npair = (m + 1) / 2;
+    for (int k = warp; k < nh; k += kWarps) {
+        for (int j = lane; j < npair; j += 32) {
+            C a = src[(size_t)k * m + 2 * j];
+            C b = 2 * j + 1 < m ? src[(size_t)k * m + 2 * j + 1] : cmk<C>(0, 0);
+            if (k == 0 || 2 * k == P) { a.y = 0; b.y = 0; }
+            F[j * RS + k] = cmk<C>(a.x - b.y, a.y + b.x);
+            if (k != 0 && 2 * k != P) {
+                const C ac = cconj(a), bc = cconj(b);
+                F[j * RS + P - k] = cmk<C>(ac.x - bc.y, ac.y + bc.x);
             }
         }
-        __syncwarp();
     }
-    if (part) {
-        const double s = block_sum<T>(acc, red);
-        if (threadIdx.x == 0) part[(size_t)f * g.NPout + pp] = s;
+}
+
+template <typename T, typename TIn, int PC>
+__global__ void __launch_bounds__(kThreads, TOMO_MIN_BLOCKS)
+k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T>* __restrict__ Y1T,
+                  const TIn* __restrict__ xin, const double* __restrict__ noise_var, TIn* __restrict__ y,
+                  CgVecs cg, const cplx_t<T>* __restrict__ twg) {
+    using C = cplx_t<T>;
+    constexpr int G = kFftGroup;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kWarps];
+    const int P = g.plan.P, m = g.m, nh = g.nh, RS = row_stride(P);
+    const int npair = (m + 1) / 2;
+    const int ngrp = (npair + G - 1) / G;
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* scr = tw + P;
+    C* F = scr + (Fused<PC>::ok ? 0 : kWarps * P);
+    const int pp = blockIdx.x, f = blockIdx.y;
+    if (st && !st[f].active) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
+    if (npair < ngrp * G)
+        for (int i = threadIdx.x; i < (ngrp * G - npair) * RS; i += blockDim.x) F[npair * RS + i] = cmk<C>(0, 0);
+    load_row_pairs<C>(Y1T + ((size_t)f * g.NPout + pp) * nh * m, m, P, nh, RS, F);
+    __syncthreads();
+    for (int gi = warp; gi < ngrp; gi += kWarps) fft_g<PC, C, false>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane);
+    __syncthreads();
+    // gather the valid outputs (W_s), add the noise term, CG dot products
+    const size_t vbase = ((size_t)f * g.NPout + pp) * mt.n_vs;
+    const TIn nv = (TIn)noise_var[pp];
+    const bool cgm = cg.p != nullptr;
+    double acc = 0.0, acc_r = 0.0, acc_a = 0.0;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+        const int rc = mt.rowcol[e];
+        const int row = rc >> 16, col = rc & 0xffff;
+        const T v = reinterpret_cast<const T*>(F + (row >> 1) * RS + col)[row & 1];
+        const TIn xi = xin[vbase + e];
+        const TIn out = (TIn)v + nv * xi;
+        y[vbase + e] = out;
+        if (cgm) {
+            acc += (double)xi * (double)out;
+            acc_r += (double)cg.r[vbase + e] * (double)out;
+            acc_a += (double)out * (double)out;
+        }
+    }
+    if (cgm) {
+        double* dp = cg.dot_part + ((size_t)f * g.NPout + pp) * 3;
+        const double s0 = block_sum<T>(acc, red);
+        if (threadIdx.x == 0) dp[0] = s0;
+        const double s1 = block_sum<T>(acc_r, red);
+        if (threadIdx.x == 0) dp[1] = s1;
+        const double s2 = block_sum<T>(acc_a, red);
+        if (threadIdx.x == 0) dp[2] = s2;
     }
 }
 
 template <typename T, typename TIn>
 cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const FrameState* st,
-                            const cplx_t<T>* Y1T, const TIn* xin, const double* noise_var, TIn* y, double* part,
+                            const cplx_t<T>* Y1T, const TIn* xin, const double* noise_var, TIn* y, const CgVecs* cg,
                             const cplx_t<T>* tw) {
-    using C = cplx_t<T>;
-    const size_t smem = sizeof(C) * ((size_t)g.plan.P * (1 + 2 * kWarps) + (size_t)g.nh * g.m);
-    auto kern = k_rows_inv_masked<T, TIn>;
+    const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const size_t smem = rows_smem<T>(g, g.m);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
-    kern<<<dim3(g.NPout, B), kThreads, smem, L.stream>>>(g, mt, st, Y1T, xin, noise_var, y, part, tw);
+#define TOMO_L(PC)                                                                                   \
+    k_rows_inv_masked<T, TIn, PC><<<dim3(g.NPout, B), kThreads, smem, L.stream>>>(g, mt, st, Y1T, xin, \
+                                                                                  noise_var, y, cgv, tw)
+    TOMO_DISPATCH_P(g.plan.P, TOMO_L)
+#undef TOMO_L
     count(L);
     return cudaGetLastError();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, int PC>
+__global__ void __launch_bounds__(kThreads, TOMO_MIN_BLOCKS)
 k_rows_inv_dense(MvmGeom g, const cplx_t<T>* __restrict__ Y1T, T* __restrict__ Yd, const cplx_t<T>* __restrict__ twg) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = g.plan.P, m = g.m, nh = g.nh;
+    constexpr int G = kFftGroup;
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* wbuf = tw + P;
-    C* S = wbuf + kWarps * 2 * P;
+    C* S = wbuf + kWarps * (G + 1) * P;
     const int pp = blockIdx.x, f = blockIdx.y;
     for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
     const C* src = Y1T + ((size_t)f * g.NPout + pp) * nh * m;
     for (int i = threadIdx.x; i < nh * m; i += blockDim.x) S[i] = src[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C* buf = wbuf + warp * 2 * P;
+    C* wb = wbuf + warp * (G + 1) * P;
     T* out = Yd + ((size_t)f * g.NPout + pp) * m * m;
-    for (int r = 2 * warp; r < m; r += 2 * kWarps) {
-        pack_row_pair<C>(S, m, r, P, nh, buf, lane);
+    for (int r0 = 2 * G * warp; r0 < m; r0 += 2 * G * kWarps) {
+        for (int gi = 0; gi < G; ++gi) {
+            const int r = r0 + 2 * gi;
+            if (r < m) pack_row_pair<C>(S, m, r, P, nh, wb + gi * P, lane);
+            else for (int k = lane; k < P; k += 32) wb[gi * P + k] = cmk<C>(0, 0);
+        }
         __syncwarp();
-        fft_warp<C>(buf, buf + P, g.plan, tw, false, lane, 32);
-        for (int c = lane; c < m; c += 32) {
-            out[(size_t)r * m + c] = buf[c].x;
-            if (r + 1 < m) out[(size_t)(r + 1) * m + c] = buf[c].y;
+        fft_g<PC, C, false>(wb, P, G, g.plan, tw, wb + G * P, lane);
+        for (int gi = 0; gi < G; ++gi) {
+            const int r = r0 + 2 * gi;
+            if (r >= m) break;
+            const C* buf = wb + gi * P;
+            for (int c = lane; c < m; c += 32) {
+                out[(size_t)r * m + c] = buf[c].x;
+                if (r + 1 < m) out[(size_t)(r + 1) * m + c] = buf[c].y;
+            }
         }
         __syncwarp();
     }
@@ -381,10 +475,11 @@ k_rows_inv_dense(MvmGeom g, const cplx_t<T>* __restrict__ Y1T, T* __restrict__ Y
 template <typename T>
 cudaError_t rows_inv_dense(const Launch& L, const MvmGeom& g, int B, const cplx_t<T>* Y1T, T* Yd, const cplx_t<T>* tw) {
     using C = cplx_t<T>;
-    const size_t smem = sizeof(C) * ((size_t)g.plan.P * (1 + 2 * kWarps) + (size_t)g.nh * g.m);
-    auto kern = k_rows_inv_dense<T>;
+    const size_t smem = sizeof(C) * ((size_t)g.plan.P * (1 + (kFftGroup + 1) * kWarps) + (size_t)g.nh * g.m);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
-    kern<<<dim3(g.NPout, B), kThreads, smem, L.stream>>>(g, Y1T, Yd, tw);
+#define TOMO_L(PC) k_rows_inv_dense<T, PC><<<dim3(g.NPout, B), kThreads, smem, L.stream>>>(g, Y1T, Yd, tw)
+    TOMO_DISPATCH_P(g.plan.P, TOMO_L)
+#undef TOMO_L
     count(L);
     return cudaGetLastError();
 }
@@ -396,7 +491,7 @@ constexpr int kVecThreads = 256;
 
 __global__ void __launch_bounds__(kVecThreads)
 k_cg_init(int N, int nparts, const float* __restrict__ s, const float* __restrict__ Ax0, float* __restrict__ x,
-          float* __restrict__ r, float* __restrict__ p, double* __restrict__ parts) {
+          float* __restrict__ r, float* __restrict__ p, float* __restrict__ Ap, double* __restrict__ parts) {
     __shared__ double red[kVecThreads / 32];
     const int f = blockIdx.y;
     const size_t base = (size_t)f * N;
@@ -407,6 +502,7 @@ k_cg_init(int N, int nparts, const float* __restrict__ s, const float* __restric
         if (!Ax0) x[base + i] = 0.f;
         r[base + i] = ri;
         p[base + i] = 0.f;
+        Ap[base + i] = 0.f;
         rr += (double)ri * ri;
         ss += (double)si * si;
     }
@@ -417,8 +513,8 @@ k_cg_init(int N, int nparts, const float* __restrict__ s, const float* __restric
 }
 
 cudaError_t cg_init(const Launch& L, int B, int N, int nparts, const float* s, const float* Ax0, float* x, float* r,
-                    float* p, double* parts) {
-    k_cg_init<<<dim3(nparts, B), kVecThreads, 0, L.stream>>>(N, nparts, s, Ax0, x, r, p, parts);
+                    float* p, float* Ap, double* parts) {
+    k_cg_init<<<dim3(nparts, B), kVecThreads, 0, L.stream>>>(N, nparts, s, Ax0, x, r, p, Ap, parts);
     count(L);
     return cudaGetLastError();
 }
@@ -433,6 +529,7 @@ __global__ void k_cg_init_scalars(int B, int nparts, const double* __restrict__ 
     }
     FrameState s;
     s.rr = rr;
+    s.alpha = 0.0;
     s.beta = 0.0;
     s.snorm2 = ss;
     s.tol2 = tol * tol * ss;
@@ -451,70 +548,50 @@ cudaError_t cg_init_scalars(const Launch& L, int B, int nparts, const double* pa
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kVecThreads)
-k_cg_update(int N, int NP, int nparts, const float* __restrict__ p, const float* __restrict__ Ap,
-            float* __restrict__ x, float* __restrict__ r, const double* __restrict__ pAp_part,
-            double* __restrict__ rr_part, const FrameState* __restrict__ st) {
-    __shared__ double red[kVecThreads / 32];
-    const int f = blockIdx.y;
-    if (!st[f].active) return;
-    double pAp = 0.0;
-    for (int i = 0; i < NP; ++i) pAp += pAp_part[(size_t)f * NP + i];
-    const bool ok = pAp > 0.0 && isfinite(pAp);
-    const float alpha = ok ? (float)(st[f].rr / pAp) : 0.f;
-    const size_t base = (size_t)f * N;
-    double rr = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        float ri = r[base + i];
-        if (ok) {
-            x[base + i] += alpha * p[base + i];
-            ri -= alpha * Ap[base + i];
-            r[base + i] = ri;
-        }
-        rr += (double)ri * ri;
-    }
-    const double s = block_sum<float>(rr, red);
-    if (threadIdx.x == 0) rr_part[(size_t)f * nparts + blockIdx.x] = s;
-}
-
-cudaError_t cg_update(const Launch& L, int B, int N, int NP, int nparts, const float* p, const float* Ap, float* x,
-                      float* r, const double* pAp_part, double* rr_part, const FrameState* st) {
-    k_cg_update<<<dim3(nparts, B), kVecThreads, 0, L.stream>>>(N, NP, nparts, p, Ap, x, r, pAp_part, rr_part, st);
-    count(L);
-    return cudaGetLastError();
-}
-
-__global__ void k_cg_scalars(int B, int NP, int nparts, const double* __restrict__ pAp_part,
-                             const double* __restrict__ rr_part, int maxit, FrameState* st) {
+// One thread per frame.  rr_part holds r^T r of the residual that the row-forward
+// pass of this iteration produced (r_k), dot_part the sums p^T Ap, r^T Ap,
+// Ap^T Ap of this iteration's product.  Stops the frame when r_k is small
+// enough (x_k is then final); otherwise alpha_k = r_k^T r_k / p^T Ap and
+// beta_{k+1} = r_{k+1}^T r_{k+1} / r_k^T r_k with the recurrence value
+// r_{k+1}^T r_{k+1} = r_k^T r_k - 2 alpha r_k^T Ap + alpha^2 Ap^T Ap.
+__global__ void k_cg_scalars(int B, int NP, const double* __restrict__ rr_part, const double* __restrict__ dot_part,
+                             FrameState* st) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= B || !st[f].active) return;
-    double pAp = 0.0, rr = 0.0;
-    for (int i = 0; i < NP; ++i) pAp += pAp_part[(size_t)f * NP + i];
-    for (int i = 0; i < nparts; ++i) rr += rr_part[(size_t)f * nparts + i];
+    double rr = 0.0, pAp = 0.0, rAp = 0.0, ApAp = 0.0;
+    for (int i = 0; i < NP; ++i) {
+        rr += rr_part[(size_t)f * NP + i];
+        const double* d = dot_part + ((size_t)f * NP + i) * 3;
+        pAp += d[0];
+        rAp += d[1];
+        ApAp += d[2];
+    }
     FrameState s = st[f];
+    s.rr = rr;
+    s.relres = sqrt(rr / s.snorm2);
+    if (rr <= s.tol2) {
+        s.active = 0;
+        s.status = 0;
+        st[f] = s;
+        return;
+    }
     if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(rr)) {
         s.active = 0;
         s.status = 2;  // TOMO_FRAME_BREAKDOWN
         st[f] = s;
         return;
     }
+    const double alpha = rr / pAp;
+    double rr_next = rr - 2.0 * alpha * rAp + alpha * alpha * ApAp;
+    if (!(rr_next > 0.0)) rr_next = 0.0;
+    s.alpha = alpha;
+    s.beta = rr_next / rr;
     s.iters += 1;
-    s.beta = rr / s.rr;
-    s.rr = rr;
-    s.relres = sqrt(rr / s.snorm2);
-    if (rr <= s.tol2) {
-        s.active = 0;
-        s.status = 0;
-    } else if (s.iters >= maxit) {
-        s.active = 0;
-        s.status = 1;  // TOMO_FRAME_MAXIT
-    }
     st[f] = s;
 }
 
-cudaError_t cg_scalars(const Launch& L, int B, int NP, int nparts, const double* pAp_part, const double* rr_part,
-                       int maxit, FrameState* st) {
-    k_cg_scalars<<<(B + 127) / 128, 128, 0, L.stream>>>(B, NP, nparts, pAp_part, rr_part, maxit, st);
+cudaError_t cg_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_part, FrameState* st) {
+    k_cg_scalars<<<(B + 127) / 128, 128, 0, L.stream>>>(B, NP, rr_part, dot_part, st);
     count(L);
     return cudaGetLastError();
 }
@@ -569,6 +646,7 @@ __global__ void k_true_residual_finalize(int B, int nparts, const double* __rest
             s.refinements += 1;
             s.active = 1;
             s.rr = rr;
+            s.alpha = 0.0;
             s.beta = 0.0;
         } else {
             s.status = 1;  // could not reach tol: reported as MAXIT
@@ -818,34 +896,44 @@ cudaError_t init_kernel_attributes() {
     if (e != cudaSuccess) return e;
     // the kernels also use a little static shared memory
     const int dyn = optin - 1024;
-    if ((e = allow_smem(k_rows_fwd<float, float>, dyn)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_rows_fwd<double, double>, dyn)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_cols_mul<float>, dyn)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_cols_mul<double>, dyn)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_rows_inv_masked<float, float>, dyn)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_rows_inv_masked<double, double>, dyn)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_rows_inv_dense<float>, dyn)) != cudaSuccess) return e;
+#define TOMO_A(PC)                                                                         \
+    if (e == cudaSuccess) e = allow_smem(k_rows_fwd<float, float, PC>, dyn);               \
+    if (e == cudaSuccess) e = allow_smem(k_rows_fwd<double, double, PC>, dyn);             \
+    if (e == cudaSuccess) e = allow_smem(k_cols_mul<float, PC>, dyn);                      \
+    if (e == cudaSuccess) e = allow_smem(k_cols_mul<double, PC>, dyn);                     \
+    if (e == cudaSuccess) e = allow_smem(k_rows_inv_masked<float, float, PC>, dyn);        \
+    if (e == cudaSuccess) e = allow_smem(k_rows_inv_masked<double, double, PC>, dyn);      \
+    if (e == cudaSuccess) e = allow_smem(k_rows_inv_dense<float, PC>, dyn);
+    TOMO_A(150)
+    TOMO_A(180)
+    TOMO_A(160)
+    TOMO_A(40)
+    TOMO_A(32)
+    TOMO_A(0)
+#undef TOMO_A
+    if (e != cudaSuccess) return e;
     if ((e = allow_smem(k_setup_rows, dyn)) != cudaSuccess) return e;
     if ((e = allow_smem(k_setup_cols, dyn)) != cudaSuccess) return e;
+    if ((e = init_fft_constants()) != cudaSuccess) return e;
     g_max_smem = dyn;
     return cudaSuccess;
 }
 
 // explicit instantiations
 template cudaError_t rows_fwd<float, float>(const Launch&, const MvmGeom&, const MaskTables&, int, const float*,
-                                            float*, const FrameState*, float2*, const float2*);
+                                            const CgVecs*, const FrameState*, float2*, const float2*);
 template cudaError_t rows_fwd<double, double>(const Launch&, const MvmGeom&, const MaskTables&, int, const double*,
-                                              double*, const FrameState*, double2*, const double2*);
+                                              const CgVecs*, const FrameState*, double2*, const double2*);
 template cudaError_t cols_mul<float>(const Launch&, const MvmGeom&, int, const FrameState*, const float2*, float2*,
                                      const float2*, const float2*);
 template cudaError_t cols_mul<double>(const Launch&, const MvmGeom&, int, const FrameState*, const double2*, double2*,
                                       const double2*, const double2*);
 template cudaError_t rows_inv_masked<float, float>(const Launch&, const MvmGeom&, const MaskTables&, int,
                                                    const FrameState*, const float2*, const float*, const double*,
-                                                   float*, double*, const float2*);
+                                                   float*, const CgVecs*, const float2*);
 template cudaError_t rows_inv_masked<double, double>(const Launch&, const MvmGeom&, const MaskTables&, int,
                                                      const FrameState*, const double2*, const double*, const double*,
-                                                     double*, double*, const double2*);
+                                                     double*, const CgVecs*, const double2*);
 template cudaError_t rows_inv_dense<float>(const Launch&, const MvmGeom&, int, const float2*, float*, const float2*);
 
 }  // namespace tomo

@@ -11,6 +11,9 @@ namespace tomo {
 
 constexpr int kWarps = 8;              // warps per block in the FFT kernels
 constexpr int kThreads = 32 * kWarps;
+#ifndef TOMO_MIN_BLOCKS
+#define TOMO_MIN_BLOCKS 3                  // resident blocks per SM the FFT kernels are compiled for
+#endif
 
 // Geometry of one FFT-based 2RBT product y = T x (Sec. 2.E): inputs are NPin
 // masked planes on an n x n grid, outputs NPout planes on an m x m grid, both
@@ -23,7 +26,8 @@ struct MvmGeom {
 // Per-frame CG scalars (FP64), one per frame.
 struct FrameState {
     double rr;       // r^T r of the current residual
-    double beta;     // beta applied by the next row-forward pass
+    double alpha;    // alpha applied by the next row-forward pass (x += alpha p, r -= alpha Ap)
+    double beta;     // beta applied by the next row-forward pass (p = r + beta p)
     double snorm2;   // ||s||^2
     double tol2;     // (tol ||s||)^2
     double relres;   // FP64 true relative residual (after a true-residual pass)
@@ -38,6 +42,7 @@ struct FrameState {
 struct MaskTables {
     const int* rowstart;   // [n+1]
     const int* col;        // [n_vs]
+    const int* rowcol;     // [n_vs]: row << 16 | col of each valid entry
     int n_vs;
 };
 
@@ -50,13 +55,24 @@ struct Launch {
 // opt-in maximum (once per process and device, before any launch or capture).
 cudaError_t init_kernel_attributes();
 
+// CG vectors of a batch, [B][N] each (FP32).
+struct CgVecs {
+    float* x;         // iterate (zeta)
+    float* r;         // residual
+    float* p;         // search direction
+    float* Ap;        // A p of the previous iteration
+    double* rr_part;  // [B][NP] partial sums of r^T r after the update
+    double* dot_part; // [B][NP][3] partial sums of p^T Ap, r^T Ap, Ap^T Ap
+};
+
 // --- MVM passes ---------------------------------------------------------
 // Row-forward pass: x [B][NPin][n_vs] (masked) -> X1T [B][NPin][nh][n].
-// With p != nullptr (CG mode) the pass first forms p = r + beta_f p on the fly,
-// writes it back to p, and transforms it; x is then r.
+// CG mode (cg != nullptr; x ignored): first applies the previous iteration's
+// update x += alpha p, r -= alpha Ap, forms p = r + beta p, accumulates r^T r
+// of the updated residual, and transforms p.
 template <typename T, typename TIn>
 cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B,
-                     const TIn* x, TIn* p, const FrameState* st,
+                     const TIn* x, const CgVecs* cg, const FrameState* st,
                      cplx_t<T>* X1T, const cplx_t<T>* tw);
 
 // Column pass: forward column FFT of the NPin planes, per-frequency block
@@ -67,11 +83,12 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
                      const cplx_t<T>* X1T, cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw);
 
 // Row-inverse pass to masked output (Sigma_ss): y = crop/mask(IFFT rows) +
-// noise_var[plane] * xin; pAp partial dot per (frame, plane) if part != nullptr.
+// noise_var[plane] * xin.  CG mode (cg != nullptr; xin = cg->p, y = cg->Ap):
+// also the partial sums p^T Ap, r^T Ap, Ap^T Ap per (frame, plane).
 template <typename T, typename TIn>
 cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B,
                             const FrameState* st, const cplx_t<T>* Y1T, const TIn* xin,
-                            const double* noise_var, TIn* y, double* part, const cplx_t<T>* tw);
+                            const double* noise_var, TIn* y, const CgVecs* cg, const cplx_t<T>* tw);
 
 // Row-inverse pass to a dense m x m output per plane: Yd [B][NPout][m][m].
 template <typename T>
@@ -80,14 +97,14 @@ cudaError_t rows_inv_dense(const Launch& L, const MvmGeom& g, int B, const cplx_
 
 // --- CG ---------------------------------------------------------------------
 cudaError_t cg_init(const Launch& L, int B, int N, int nparts, const float* s, const float* Ax0,
-                    float* x, float* r, float* p, double* parts);
+                    float* x, float* r, float* p, float* Ap, double* parts);
 cudaError_t cg_init_scalars(const Launch& L, int B, int nparts, const double* parts, double tol,
                             int warm, FrameState* st);
-cudaError_t cg_update(const Launch& L, int B, int N, int NP, int nparts, const float* p,
-                      const float* Ap, float* x, float* r, const double* pAp_part,
-                      double* rr_part, const FrameState* st);
-cudaError_t cg_scalars(const Launch& L, int B, int NP, int nparts, const double* pAp_part,
-                       const double* rr_part, int maxit, FrameState* st);
+// Per-frame scalars after an iteration: convergence test on the updated
+// residual, alpha, and beta of the next iteration from
+// r_new^T r_new = r^T r - 2 alpha r^T Ap + alpha^2 Ap^T Ap (Chronopoulos & Gear).
+cudaError_t cg_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_part,
+                       FrameState* st);
 cudaError_t to_f64(const Launch& L, size_t n, const float* a, double* b);
 cudaError_t true_residual(const Launch& L, int B, int N, int nparts, const float* s,
                           const double* Ax, float* r, double* parts);

@@ -55,7 +55,7 @@ FRAME_INFO_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("s
 EXPORTS = ("tomo_create", "tomo_layout", "tomo_apply_css", "tomo_apply_css_f64", "tomo_apply_cos",
            "tomo_solve", "tomo_solve_host", "tomo_launch_count", "tomo_set_kernel_timing",
            "tomo_get_kernel_timing", "tomo_destroy", "tomo_strerror")
-KERNEL_NAMES = ("rows_fwd", "cols_mul", "rows_inv", "cg_update")
+KERNEL_NAMES = ("rows_fwd", "cols_mul", "rows_inv", "cg_scalars")
 
 _lib = None
 
