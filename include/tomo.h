@@ -95,6 +95,8 @@ typedef struct {
     int fft_P;             /* padded FFT side for Sigma_ss, 0 = smallest valid    */
     int fft_Pcos;          /* padded FFT side for Sigma_phi_s, 0 = smallest valid */
     int max_batch;         /* frames per call the workspaces are sized for        */
+    int precond;           /* 1: also build the block-circulant preconditioner    */
+    double precond_floor;  /* c of the preconditioner (see tomo_solve_opts), 0 = 3 */
 } tomo_config;
 
 typedef struct {
@@ -108,11 +110,13 @@ typedef struct {
 } tomo_layout_info;
 
 typedef struct {
-    double tol;            /* target FP64 true relative residual ||s-A z||/||s|| */
+    double tol;            /* target FP64 true relative residual ||s-A z||/||s||;
+                              CG drives its recursive residual to 0.7 tol       */
     int max_iter;          /* CG iterations per call, over all refinement passes   */
     int max_refine;        /* FP64 true-residual restarts after the first pass    */
     int warm_start;        /* 1: zeta_dev holds the initial guess on entry        */
     int check_every;       /* iterations between host convergence checks (>= 1)   */
+    int precond;           /* 1: preconditioned CG with the block-circulant M     */
 } tomo_solve_opts;
 
 typedef struct {
@@ -125,7 +129,17 @@ typedef struct {
 
 typedef struct tomo_handle tomo_handle;
 
-/* Builds geometry, the Sigma_ss and Sigma_phi_s generator vectors (FP64, on
+/* Preconditioner (an addition to the paper, which runs its solvers without
+ * one, Sec. 2.G): M^{-1} = W_s F^{-1} M(f) F W_s^T with, per frequency f of
+ * the P x P torus, M(f) = (K_+(f) + c diag(sigma_g^2))^{-1}, K(f) the
+ * (2 nGS) x (2 nGS) Hermitian block of the spectrum of Sigma_ss's covariance
+ * evaluated at every lag of the torus (periodised), K_+ its eigenvalues
+ * clamped at zero.  It is the block-circulant approximation of
+ * (Sigma_ss + Sigma_eta_eta)^{-1} and costs one more FFT round trip per
+ * iteration.  Used by tomo_solve when both cfg->precond and opts->precond are
+ * set.
+ *
+ * Builds geometry, the Sigma_ss and Sigma_phi_s generator vectors (FP64, on
  * the device) and their spectra (Sec. 2.E: the FFT of the unique-element
  * vector is computed once, offline).  cuda_stream may be NULL (legacy default
  * stream).  Returns TOMO_EINVAL for an inconsistent configuration, e.g. a
@@ -161,7 +175,8 @@ tomo_status tomo_apply_cos(tomo_handle* h, const float* zeta_dev, float* phase_d
  * Eq. SAap2.  slopes_dev [batch][N]; zeta_dev [batch][N] (warm start in if
  * opts->warm_start); phase_dev [batch][n_targets][n_vphi] or NULL to skip the
  * projection; info_host [batch] host memory or NULL.  opts NULL = defaults
- * (tol 1e-4, max_iter 10000, max_refine 2, cold start, check_every 32).
+ * (tol 1e-4, max_iter 10000, max_refine 2, cold start, check_every 32, no
+ * preconditioner).
  * Synchronises the stream at each convergence check. */
 tomo_status tomo_solve(tomo_handle* h, const float* slopes_dev, int batch,
                        const tomo_solve_opts* opts, float* zeta_dev, float* phase_dev,

@@ -27,7 +27,7 @@ using namespace tomo;
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int B = -1, iters = 0;
+    int B = -1, iters = 0, mode = 0;
     long long nodes = 0;
 };
 
@@ -57,16 +57,18 @@ struct tomo_handle {
     float2* d_K32 = nullptr;
     double2* d_K64 = nullptr;
     float2* d_Kc32 = nullptr;
+    float2* d_M32 = nullptr;           // block-circulant preconditioner spectra (nullptr: not built)
+    double* d_zero_var = nullptr;      // zero diagonal for the preconditioner pass
     int* d_iidx = nullptr;
     float* d_iw = nullptr;
     // workspaces
     float2 *X1 = nullptr, *Y1 = nullptr, *Xc = nullptr, *Yc = nullptr;
     double2 *X1d = nullptr, *Y1d = nullptr;
     float* Ydc = nullptr;
-    float *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
+    float *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr, *w = nullptr;
     double *xd = nullptr, *yd = nullptr;
     FrameState* st = nullptr;
-    double *dot_part = nullptr, *rr_part = nullptr, *init_part = nullptr, *res_part = nullptr;
+    double *dot_part = nullptr, *dot_part_M = nullptr, *rr_part = nullptr, *init_part = nullptr, *res_part = nullptr;
     int nparts = 0;
     int* d_nactive = nullptr;
     int* h_nactive = nullptr;
@@ -168,7 +170,9 @@ tomo_status apply_ss32(tomo_handle* h, const Launch& L, const float* x, float* y
     return TOMO_OK;
 }
 
-CgVecs cg_vecs(tomo_handle* h) { return CgVecs{h->x, h->r, h->p, h->Ap, h->rr_part, h->dot_part}; }
+CgVecs cg_vecs(tomo_handle* h, int mode, double* dots) {
+    return CgVecs{h->x, h->r, h->p, h->Ap, h->rr_part, dots, mode, h->z, h->w};
+}
 
 tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double* y, int B) {
     CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1d, h->d_tw64)));
@@ -192,48 +196,68 @@ tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi
 // One CG iteration on all active frames of the batch: the previous update and
 // the new direction (row-forward pass), A p (column and row-inverse passes),
 // and the per-frame scalars.
-tomo_status cg_iteration(tomo_handle* h, const Launch& L, int B) {
-    const CgVecs cg = cg_vecs(h);
-    TRY(apply_ss32(h, L, nullptr, nullptr, B, h->st, &cg));
-    CK(cg_scalars(L, B, h->NP, h->rr_part, h->dot_part, h->st));
-    return TOMO_OK;
-}
-
-// The same iteration launched eagerly with an event before and after each
-// kernel; the elapsed times are accumulated per kernel at the next sync.
-tomo_status cg_iteration_timed(tomo_handle* h, const Launch& L, int B, std::vector<std::pair<int, int>>& marks) {
-    auto mark = [&](void) -> int {
+//
+// One PCG iteration (Chronopoulos & Gear): the previous update and FFT of r
+// (row-forward), z = M^{-1} r (column pass with M, row-inverse pass with
+// r^T z), w = A z (three passes, z^T w), and the per-frame scalars.
+//
+// With marks != nullptr every kernel is bracketed by events (kernel timing).
+tomo_status iteration(tomo_handle* h, const Launch& L, int B, bool pcg, std::vector<std::pair<int, int>>* marks) {
+    int last = -1;
+    auto mark = [&](int slot) -> tomo_status {
+        if (!marks) return TOMO_OK;
         cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        if (cudaEventCreate(&e) != cudaSuccess) return TOMO_ECUDA;
         h->ev.push_back(e);
-        cudaEventRecord(e, L.stream);
-        return (int)h->ev.size() - 1;
+        if (cudaEventRecord(e, L.stream) != cudaSuccess) return TOMO_ECUDA;
+        const int id = (int)h->ev.size() - 1;
+        if (last >= 0) marks->push_back({last * 8 + slot, id});
+        last = id;
+        return TOMO_OK;
     };
-    const CgVecs cg = cg_vecs(h);
-    int e0 = mark();
-    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32)));
-    int e1 = mark();
-    CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
-    int e2 = mark();
-    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->Ap, &cg,
+    // slot encoding: pair (start event * 8 + kernel class, end event)
+    TRY(mark(0));
+    if (!pcg) {
+        const CgVecs cg = cg_vecs(h, 1, h->dot_part);
+        CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32)));
+        TRY(mark(0));
+        CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
+        TRY(mark(1));
+        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->Ap, &cg,
+                                          h->d_tw32)));
+        TRY(mark(2));
+        CK(cg_scalars(L, B, h->NP, h->rr_part, h->dot_part, h->st));
+        TRY(mark(3));
+        return TOMO_OK;
+    }
+    const CgVecs cgM = cg_vecs(h, 2, h->dot_part_M);
+    const CgVecs cgA = cg_vecs(h, 2, h->dot_part);
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cgM, h->st, h->X1, h->d_tw32)));
+    TRY(mark(0));
+    CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_M32, h->d_tw32)));
+    TRY(mark(1));
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->r, h->d_zero_var, h->z, &cgM,
                                       h->d_tw32)));
-    int e3 = mark();
-    CK(cg_scalars(L, B, h->NP, h->rr_part, h->dot_part, h->st));
-    int e4 = mark();
-    if (e0 < 0 || e1 < 0 || e2 < 0 || e3 < 0 || e4 < 0) return TOMO_ECUDA;
-    marks.push_back({e0, e1});
-    marks.push_back({e1, e2});
-    marks.push_back({e2, e3});
-    marks.push_back({e3, e4});
+    TRY(mark(2));
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, h->z, nullptr, h->st, h->X1, h->d_tw32)));
+    TRY(mark(0));
+    CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
+    TRY(mark(1));
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->z, h->d_noise_var, h->w, &cgA,
+                                      h->d_tw32)));
+    TRY(mark(2));
+    CK(pcg_scalars(L, B, h->NP, h->rr_part, h->dot_part_M, h->dot_part, h->st));
+    TRY(mark(3));
     return TOMO_OK;
 }
 
 void collect_timing(tomo_handle* h, std::vector<std::pair<int, int>>& marks) {
-    for (size_t i = 0; i < marks.size(); ++i) {
+    for (const auto& m : marks) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, h->ev[marks[i].first], h->ev[marks[i].second]) == cudaSuccess) {
-            h->kt_ms[i % 4] += ms;
-            h->kt_n[i % 4] += 1;
+        const int start = m.first / 8, slot = m.first % 8;
+        if (cudaEventElapsedTime(&ms, h->ev[start], h->ev[m.second]) == cudaSuccess) {
+            h->kt_ms[slot] += ms;
+            h->kt_n[slot] += 1;
         }
     }
     marks.clear();
@@ -241,8 +265,8 @@ void collect_timing(tomo_handle* h, std::vector<std::pair<int, int>>& marks) {
     h->ev.clear();
 }
 
-tomo_status build_graph(tomo_handle* h, int B, int iters) {
-    if (h->graph.exec && h->graph.B == B && h->graph.iters == iters) return TOMO_OK;
+tomo_status build_graph(tomo_handle* h, int B, int iters, bool pcg) {
+    if (h->graph.exec && h->graph.B == B && h->graph.iters == iters && h->graph.mode == (int)pcg) return TOMO_OK;
     if (h->graph.exec) {
         cudaGraphExecDestroy(h->graph.exec);
         h->graph.exec = nullptr;
@@ -251,7 +275,7 @@ tomo_status build_graph(tomo_handle* h, int B, int iters) {
     CK(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
     Launch Lc{h->work, &h->launches};
     tomo_status s = TOMO_OK;
-    for (int i = 0; i < iters && s == TOMO_OK; ++i) s = cg_iteration(h, Lc, B);
+    for (int i = 0; i < iters && s == TOMO_OK; ++i) s = iteration(h, Lc, B, pcg, nullptr);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->work, &graph);
     const long long nodes = h->launches - before;
@@ -266,6 +290,7 @@ tomo_status build_graph(tomo_handle* h, int B, int iters) {
     if (e != cudaSuccess) return TOMO_ECUDA;
     h->graph.B = B;
     h->graph.iters = iters;
+    h->graph.mode = (int)pcg;
     h->graph.nodes = nodes;
     return TOMO_OK;
 }
@@ -276,6 +301,7 @@ tomo_status validate(const tomo_config* c) {
         return TOMO_EINVAL;
     if (!(c->D > 0) || !(c->obstruction >= 0) || !(c->obstruction < 1) || !(c->r0 > 0) || !(c->L0 > 0))
         return TOMO_EINVAL;
+    if (!(c->precond_floor >= 0)) return TOMO_EINVAL;
     if (c->max_batch < 1 || c->max_batch > 4096) return TOMO_EINVAL;
     const double H = c->gs[0].height;
     for (int g = 0; g < c->n_gs; ++g) {
@@ -428,11 +454,34 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         TRY(dalloc(h, &h->d_K64, (size_t)npl * (h->P / 2 + 1) * h->P));
         TRY(dalloc(h, &h->d_K32, (size_t)npl * (h->P / 2 + 1) * h->P));
         CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
-        CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G));
+        CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G, false));
         CK(spectra(L, h->P, npl, h->NP, h->plan, G, H, h->d_tw64, h->d_K64, h->d_K32));
         CK(cudaStreamSynchronize(h->stream));
         cudaFree(G);
         cudaFree(H);
+    }
+    // --- block-circulant preconditioner on the same P x P torus ------------------------
+    if (c->precond) {
+        const int npl = h->NP * h->NP;
+        const size_t Gsz = (size_t)npl * h->P * h->P;
+        const size_t Ksz = (size_t)npl * (h->P / 2 + 1) * h->P;
+        double* G = nullptr;
+        double2 *H = nullptr, *K64 = nullptr;
+        CK(cudaMalloc(&G, sizeof(double) * Gsz));
+        CK(cudaMalloc(&H, sizeof(double2) * Ksz));
+        CK(cudaMalloc(&K64, sizeof(double2) * Ksz));
+        TRY(dalloc(h, &h->d_M32, Ksz));
+        TRY(dalloc(h, &h->d_zero_var, h->NP));
+        CK(cudaMemsetAsync(h->d_zero_var, 0, sizeof(double) * h->NP, h->stream));
+        CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
+        CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G, true));
+        CK(spectra(L, h->P, npl, h->NP, h->plan, G, H, h->d_tw64, K64, nullptr));
+        const double floor_c = c->precond_floor > 0 ? c->precond_floor : 3.0;
+        CK(precond_spectra(L, h->P, h->NP, K64, h->d_noise_var, floor_c, h->d_M32));
+        CK(cudaStreamSynchronize(h->stream));
+        cudaFree(G);
+        cudaFree(H);
+        cudaFree(K64);
     }
     // --- Sigma_phi_s generators and spectra, one set per target ------------------------
     {
@@ -499,6 +548,9 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     TRY(dalloc(h, &h->st, B));
     h->nparts = std::max(1, std::min(64, (h->N + 4095) / 4096));
     TRY(dalloc(h, &h->dot_part, B * h->NP * 3));
+    TRY(dalloc(h, &h->dot_part_M, B * h->NP * 3));
+    TRY(dalloc(h, &h->z, B * h->N));
+    TRY(dalloc(h, &h->w, B * h->N));
     TRY(dalloc(h, &h->rr_part, B * h->NP));
     TRY(dalloc(h, &h->res_part, B * h->nparts));
     TRY(dalloc(h, &h->init_part, B * 2 * h->nparts));
@@ -539,8 +591,13 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         CK(cg_init(L, B, h->N, h->nparts, s, nullptr, h->x, h->r, h->p, h->Ap, h->init_part));
     }
     CK(cg_init_scalars(L, B, h->nparts, h->init_part, o.tol, o.warm_start, h->st));
+    const bool pcg = o.precond && h->d_M32;
+    if (pcg) {
+        CK(cudaMemsetAsync(h->z, 0, sizeof(float) * B * h->N, h->work));
+        CK(cudaMemsetAsync(h->w, 0, sizeof(float) * B * h->N, h->work));
+    }
     const int chunk = std::max(1, o.check_every);
-    if (!h->timing) TRY(build_graph(h, B, chunk));
+    if (!h->timing) TRY(build_graph(h, B, chunk, pcg));
     long long total_iters = 0;
     std::vector<std::pair<int, int>> marks;
     for (;;) {
@@ -575,7 +632,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             break;
         }
         if (h->timing) {
-            for (int i = 0; i < chunk; ++i) TRY(cg_iteration_timed(h, L, B, marks));
+            for (int i = 0; i < chunk; ++i) TRY(iteration(h, L, B, pcg, &marks));
         } else {
             CK(cudaGraphLaunch(h->graph.exec, h->work));
             h->launches += h->graph.nodes;
@@ -609,6 +666,7 @@ tomo_solve_opts default_opts() {
     o.max_refine = 2;
     o.warm_start = 0;
     o.check_every = 32;
+    o.precond = 0;
     return o;
 }
 

@@ -78,7 +78,7 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
     const size_t vbase = ((size_t)f * g.NPin + q) * mt.n_vs;
     const bool cgm = cg.p != nullptr;
     double rr = 0.0;
-    if (cgm) {
+    if (cgm && cg.mode == 1) {
         const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
 #pragma unroll 4
         for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
@@ -98,6 +98,27 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
             const int row = rc >> 16, col = rc & 0xffff;
             T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
             *dst = (T)pn;
+        }
+    } else if (cgm) {
+        const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+            const size_t i = vbase + e;
+            const int rc = mt.rowcol[e];
+            const float pn = cg.z[i] + beta * cg.p[i];
+            const float sn = cg.w[i] + beta * cg.Ap[i];
+            float re = cg.r[i];
+            if (alpha != 0.f) {
+                cg.x[i] += alpha * pn;
+                re -= alpha * sn;
+                cg.r[i] = re;
+            }
+            cg.p[i] = pn;
+            cg.Ap[i] = sn;
+            rr += (double)re * re;
+            const int row = rc >> 16, col = rc & 0xffff;
+            T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
+            *dst = (T)re;
         }
     } else {
 #pragma unroll 4
@@ -141,7 +162,7 @@ size_t rows_smem(const MvmGeom& g, int nrows) {
 template <typename T, typename TIn>
 cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const TIn* x, const CgVecs* cg,
                      const FrameState* st, cplx_t<T>* X1T, const cplx_t<T>* tw) {
-    const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     const size_t smem = rows_smem<T>(g, g.n);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
 #define TOMO_L(PC) k_rows_fwd<T, TIn, PC><<<dim3(g.NPin, B), kThreads, smem, L.stream>>>(g, mt, x, cgv, st, X1T, tw)
@@ -421,7 +442,7 @@ template <typename T, typename TIn>
 cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const FrameState* st,
                             const cplx_t<T>* Y1T, const TIn* xin, const double* noise_var, TIn* y, const CgVecs* cg,
                             const cplx_t<T>* tw) {
-    const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     const size_t smem = rows_smem<T>(g, g.m);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
 #define TOMO_L(PC)                                                                                   \
@@ -519,6 +540,8 @@ cudaError_t cg_init(const Launch& L, int B, int N, int nparts, const float* s, c
     return cudaGetLastError();
 }
 
+constexpr double kInnerTol = 0.7;
+
 __global__ void k_cg_init_scalars(int B, int nparts, const double* __restrict__ parts, double tol, FrameState* st) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= B) return;
@@ -532,12 +555,17 @@ __global__ void k_cg_init_scalars(int B, int nparts, const double* __restrict__ 
     s.alpha = 0.0;
     s.beta = 0.0;
     s.snorm2 = ss;
-    s.tol2 = tol * tol * ss;
+    // the recursive (FP32) residual is driven below kInnerTol * tol so that the
+    // FP64 true residual normally clears tol without a restart
+    s.tol2 = (kInnerTol * tol) * (kInnerTol * tol) * ss;
     s.relres = ss > 0.0 ? sqrt(rr / ss) : 0.0;
     s.iters = 0;
     s.active = (ss > 0.0 && rr > s.tol2) ? 1 : 0;
     s.status = 0;
     s.refinements = 0;
+    s.gamma = 0.0;
+    s.fresh = 1;
+    s.pad_ = 0;
     st[f] = s;
 }
 
@@ -596,6 +624,51 @@ cudaError_t cg_scalars(const Launch& L, int B, int NP, const double* rr_part, co
     return cudaGetLastError();
 }
 
+__global__ void k_pcg_scalars(int B, int NP, const double* __restrict__ rr_part, const double* __restrict__ dot_M,
+                              const double* __restrict__ dot_A, FrameState* st) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= B || !st[f].active) return;
+    double rr = 0.0, gamma = 0.0, delta = 0.0;
+    for (int i = 0; i < NP; ++i) {
+        rr += rr_part[(size_t)f * NP + i];
+        gamma += dot_M[((size_t)f * NP + i) * 3];
+        delta += dot_A[((size_t)f * NP + i) * 3];
+    }
+    FrameState s = st[f];
+    s.rr = rr;
+    s.relres = sqrt(rr / s.snorm2);
+    if (rr <= s.tol2) {
+        s.active = 0;
+        s.status = 0;
+        st[f] = s;
+        return;
+    }
+    double beta = 0.0, den = delta;
+    if (!s.fresh) {
+        beta = gamma / s.gamma;
+        den = delta - beta * gamma / s.alpha;
+    }
+    if (!(gamma > 0.0) || !(den > 0.0) || !isfinite(gamma) || !isfinite(den)) {
+        s.active = 0;
+        s.status = 2;  // TOMO_FRAME_BREAKDOWN
+        st[f] = s;
+        return;
+    }
+    s.alpha = gamma / den;
+    s.beta = beta;
+    s.gamma = gamma;
+    s.fresh = 0;
+    s.iters += 1;
+    st[f] = s;
+}
+
+cudaError_t pcg_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_M,
+                        const double* dot_A, FrameState* st) {
+    k_pcg_scalars<<<(B + 127) / 128, 128, 0, L.stream>>>(B, NP, rr_part, dot_M, dot_A, st);
+    count(L);
+    return cudaGetLastError();
+}
+
 __global__ void k_to_f64(size_t n, const float* __restrict__ a, double* __restrict__ b) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         b[i] = (double)a[i];
@@ -648,6 +721,7 @@ __global__ void k_true_residual_finalize(int B, int nparts, const double* __rest
             s.rr = rr;
             s.alpha = 0.0;
             s.beta = 0.0;
+            s.fresh = 1;
         } else {
             s.status = 1;  // could not reach tol: reported as MAXIT
         }
@@ -705,15 +779,14 @@ __device__ double vk_shape(double x, const VkParams& vk) {
 // model, Appendix A.2; cone factor per layer, Sec. 2.D).  Stored at the
 // wrapped lag (di mod P, dj mod P) so that y = IFFT(FFT(t) FFT(x)) is the
 // linear convolution y(a) = sum_b t(a - b) x(b) on the n x n grid.
-__global__ void k_gen_css(int n, int P, int NP, double d, int n_layers, const LayerGeom* __restrict__ layers,
+__global__ void k_gen_css(int lo, int span, int P, int NP, double d, int n_layers, const LayerGeom* __restrict__ layers,
                           const double* __restrict__ alpha, VkParams vk, double* __restrict__ G) {
-    const int span = 2 * n - 1;
     const int li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= span * span) return;
     const int pair = blockIdx.y;
     const int p = pair / NP, q = pair % NP;
     const int gp = p >> 1, cp = p & 1, gq = q >> 1, cq = q & 1;
-    const int di = li / span - (n - 1), dj = li % span - (n - 1);
+    const int di = li / span + lo, dj = li % span + lo;
     const double opx = cp == 0 ? 0.5 * d : 0.0, opy = cp == 1 ? 0.5 * d : 0.0;
     const double oqx = cq == 0 ? 0.5 * d : 0.0, oqy = cq == 1 ? 0.5 * d : 0.0;
     const double dax = alpha[2 * gp] - alpha[2 * gq], day = alpha[2 * gp + 1] - alpha[2 * gq + 1];
@@ -735,10 +808,12 @@ __global__ void k_gen_css(int n, int P, int NP, double d, int n_layers, const La
 }
 
 cudaError_t gen_css(const Launch& L, int n, int P, int NP, double d, int n_layers, const LayerGeom* layers,
-                    const double* gs_alpha, VkParams vk, double* G) {
-    const int span = 2 * n - 1;
-    k_gen_css<<<dim3((span * span + 127) / 128, NP * NP), 128, 0, L.stream>>>(n, P, NP, d, n_layers, layers, gs_alpha,
-                                                                            vk, G);
+                    const double* gs_alpha, VkParams vk, double* G, bool periodised) {
+    // exact 2RBT generator: lags [-(n-1), n-1]; periodised: every lag of the P-torus, [-P/2, P/2)
+    const int lo = periodised ? -(P / 2) : -(n - 1);
+    const int span = periodised ? P : 2 * n - 1;
+    k_gen_css<<<dim3((span * span + 127) / 128, NP * NP), 128, 0, L.stream>>>(lo, span, P, NP, d, n_layers, layers,
+                                                                            gs_alpha, vk, G);
     count(L);
     return cudaGetLastError();
 }
@@ -856,6 +931,120 @@ cudaError_t spectra(const Launch& L, int P, int npl, int NPin, const FftPlan& pl
     count(L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_setup_cols<<<npl, kThreads, smem, L.stream>>>(plan, NPin, npl, H, tw64, K64, K32);
+    count(L);
+    return cudaGetLastError();
+}
+
+// Block-circulant preconditioner (per frequency f of the P x P torus):
+//   M(f) = (K_+(f) + c Sigma)^{-1} / P^2,
+// K(f) the 12 x 12 (NP x NP) Hermitian block of the periodised generator's
+// spectrum, K_+ its eigenvalues clamped at zero (the periodised kernel is not
+// exactly positive semi-definite), Sigma = diag(sigma_p^2).  One thread per
+// frequency, FP64: cyclic Jacobi (Golub & Van Loan, Matrix Computations, 8.5)
+// on the real symmetric embedding [[Re K, -Im K], [Im K, Re K]], then a
+// Cholesky inverse of the clamped, shifted embedding.  M is written in the
+// layout of the spectra, [kx][q][ky][p].
+constexpr int kMaxNP = 16;
+__global__ void k_precond(int P, int NP, const double2* __restrict__ K64, const double* __restrict__ noise_var,
+                          double floor_c, double scale, float2* __restrict__ M32) {
+    // K64 holds FFT(t) / P^2 (the inverse-transform normalisation folded in); undo it here
+    const double kscale = (double)P * (double)P;
+    const int nh = P / 2 + 1;
+    const int fi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fi >= nh * P) return;
+    const int kx = fi / P, ky = fi % P;
+    const int n2 = 2 * NP;
+    double R[2 * kMaxNP][2 * kMaxNP], V[2 * kMaxNP][2 * kMaxNP];
+    for (int p = 0; p < NP; ++p)
+        for (int q = 0; q < NP; ++q) {
+            const double2 a = K64[(((size_t)kx * NP + q) * P + ky) * NP + p];
+            const double2 b = K64[(((size_t)kx * NP + p) * P + ky) * NP + q];
+            const double re = 0.5 * kscale * (a.x + b.x), im = 0.5 * kscale * (a.y - b.y);   // (K + K^H) / 2
+            R[p][q] = re;
+            R[p + NP][q + NP] = re;
+            R[p + NP][q] = im;
+            R[p][q + NP] = -im;
+        }
+    for (int i = 0; i < n2; ++i)
+        for (int j = 0; j < n2; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n2; ++i)
+            for (int j = 0; j < n2; ++j) {
+                tot += R[i][j] * R[i][j];
+                if (i != j) off += R[i][j] * R[i][j];
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < n2 - 1; ++p)
+            for (int q = p + 1; q < n2; ++q) {
+                const double apq = R[p][q];
+                if (fabs(apq) <= 1e-300) continue;
+                const double theta = (R[q][q] - R[p][p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n2; ++k) {        // columns p, q of R
+                    const double rkp = R[k][p], rkq = R[k][q];
+                    R[k][p] = c * rkp - s * rkq;
+                    R[k][q] = s * rkp + c * rkq;
+                }
+                for (int k = 0; k < n2; ++k) {        // rows p, q of R
+                    const double rpk = R[p][k], rqk = R[q][k];
+                    R[p][k] = c * rpk - s * rqk;
+                    R[q][k] = s * rpk + c * rqk;
+                }
+                for (int k = 0; k < n2; ++k) {        // eigenvectors
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    // R <- V max(Lambda, 0) V^T + c Sigma
+    double lam[2 * kMaxNP];
+    for (int i = 0; i < n2; ++i) lam[i] = R[i][i] > 0.0 ? R[i][i] : 0.0;
+    for (int i = 0; i < n2; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < n2; ++k) acc += V[i][k] * lam[k] * V[j][k];
+            R[i][j] = acc;
+        }
+    for (int i = 0; i < n2; ++i) R[i][i] += floor_c * noise_var[i % NP];
+    // Cholesky R = L L^T in the lower triangle, then R^{-1} = L^{-T} L^{-1} into V
+    for (int j = 0; j < n2; ++j) {
+        double dsum = R[j][j];
+        for (int k = 0; k < j; ++k) dsum -= R[j][k] * R[j][k];
+        const double ljj = sqrt(dsum > 0.0 ? dsum : 1e-300);
+        R[j][j] = ljj;
+        for (int i = j + 1; i < n2; ++i) {
+            double acc = R[i][j];
+            for (int k = 0; k < j; ++k) acc -= R[i][k] * R[j][k];
+            R[i][j] = acc / ljj;
+        }
+    }
+    for (int col = 0; col < n2; ++col) {
+        double y[2 * kMaxNP];
+        for (int i = 0; i < n2; ++i) {            // L y = e_col
+            double acc = i == col ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) acc -= R[i][k] * y[k];
+            y[i] = acc / R[i][i];
+        }
+        for (int i = n2 - 1; i >= 0; --i) {       // L^T x = y
+            double acc = y[i];
+            for (int k = i + 1; k < n2; ++k) acc -= R[k][i] * V[k][col];
+            V[i][col] = acc / R[i][i];
+        }
+    }
+    for (int p = 0; p < NP; ++p)
+        for (int q = 0; q < NP; ++q)
+            M32[(((size_t)kx * NP + q) * P + ky) * NP + p] =
+                make_float2((float)(V[p][q] * scale), (float)(V[p + NP][q] * scale));
+}
+
+cudaError_t precond_spectra(const Launch& L, int P, int NP, const double2* K64, const double* noise_var,
+                            double floor_c, float2* M32) {
+    if (NP > kMaxNP) return cudaErrorInvalidValue;
+    const int nf = (P / 2 + 1) * P;
+    k_precond<<<(nf + 63) / 64, 64, 0, L.stream>>>(P, NP, K64, noise_var, floor_c, 1.0 / ((double)P * P), M32);
     count(L);
     return cudaGetLastError();
 }

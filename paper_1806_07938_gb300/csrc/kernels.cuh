@@ -35,6 +35,9 @@ struct FrameState {
     int active;      // 1 while CG runs on this frame
     int status;      // TOMO_FRAME_*
     int refinements; // restarts from the true residual
+    double gamma;    // PCG: r^T M^{-1} r of the previous iteration
+    int fresh;       // PCG: 1 on the first iteration after a (re)start
+    int pad_;
 };
 
 // Masked-vector index tables: valid entries of row r are [rowstart[r], rowstart[r+1]),
@@ -56,13 +59,20 @@ struct Launch {
 cudaError_t init_kernel_attributes();
 
 // CG vectors of a batch, [B][N] each (FP32).
+//   mode 1 (CG):  row-forward applies x += alpha p, r -= alpha Ap, p = r + beta p and transforms p;
+//   mode 2 (PCG, Chronopoulos-Gear form): row-forward applies p = z + beta p,
+//                 s = w + beta s, x += alpha p, r -= alpha s and transforms r;
+//                 z = M^{-1} r and w = A z come from the two products of the iteration.
 struct CgVecs {
     float* x;         // iterate (zeta)
     float* r;         // residual
     float* p;         // search direction
-    float* Ap;        // A p of the previous iteration
+    float* Ap;        // CG: A p of the previous iteration; PCG: s, the recurrence for A p
     double* rr_part;  // [B][NP] partial sums of r^T r after the update
-    double* dot_part; // [B][NP][3] partial sums of p^T Ap, r^T Ap, Ap^T Ap
+    double* dot_part; // [B][NP][3] partial sums xin^T y, r^T y, y^T y of the row-inverse pass
+    int mode;
+    float* z;         // PCG: M^{-1} r
+    float* w;         // PCG: A z
 };
 
 // --- MVM passes ---------------------------------------------------------
@@ -105,6 +115,12 @@ cudaError_t cg_init_scalars(const Launch& L, int B, int nparts, const double* pa
 // r_new^T r_new = r^T r - 2 alpha r^T Ap + alpha^2 Ap^T Ap (Chronopoulos & Gear).
 cudaError_t cg_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_part,
                        FrameState* st);
+// PCG scalars (Chronopoulos & Gear): gamma = r^T z, delta = z^T A z,
+// beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old);
+// dot_M from the preconditioner pass (xin = r, y = z), dot_A from the
+// operator pass (xin = z, y = w).
+cudaError_t pcg_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_M,
+                        const double* dot_A, FrameState* st);
 cudaError_t to_f64(const Launch& L, size_t n, const float* a, double* b);
 cudaError_t true_residual(const Launch& L, int B, int N, int nparts, const float* s,
                           const double* Ax, float* r, double* parts);
@@ -129,8 +145,14 @@ struct LayerGeom {
 };
 
 // Sigma_ss generators on the wrapped P x P grid: G[p*NP+q][P][P] (pre-zeroed).
+// periodised = false: the exact 2RBT generator, lags [-(n-1), n-1];
+// periodised = true: the covariance at every lag of the P-torus, [-P/2, P/2).
 cudaError_t gen_css(const Launch& L, int n, int P, int NP, double d, int n_layers,
-                    const LayerGeom* layers, const double* gs_alpha, VkParams vk, double* G);
+                    const LayerGeom* layers, const double* gs_alpha, VkParams vk, double* G, bool periodised);
+// Block-circulant preconditioner spectra M(f) = (K_+(f) + c diag(sigma^2))^{-1} / P^2
+// from the FP64 spectra of the periodised generator (both [nh][NP][P][NP]).
+cudaError_t precond_spectra(const Launch& L, int P, int NP, const double2* K64, const double* noise_var,
+                            double floor_c, float2* M32);
 // Sigma_phi_s generators of one target: G[k*NP+q][P][P] for the m x n 2RBT blocks.
 cudaError_t gen_cos(const Launch& L, int n, int m, int P, int NP, double d, int n_layers,
                     const LayerGeom* layers, const double* gs_alpha, double bx, double by,

@@ -31,7 +31,8 @@ class tomo_config(ctypes.Structure):
                 ("r0", ctypes.c_double), ("L0", ctypes.c_double),
                 ("n_targets", ctypes.c_int), ("target_x", ctypes.POINTER(ctypes.c_double)),
                 ("target_y", ctypes.POINTER(ctypes.c_double)),
-                ("fft_P", ctypes.c_int), ("fft_Pcos", ctypes.c_int), ("max_batch", ctypes.c_int)]
+                ("fft_P", ctypes.c_int), ("fft_Pcos", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("precond", ctypes.c_int), ("precond_floor", ctypes.c_double)]
 
 
 class tomo_layout_info(ctypes.Structure):
@@ -41,7 +42,7 @@ class tomo_layout_info(ctypes.Structure):
 
 class tomo_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 class tomo_frame_info(ctypes.Structure):
@@ -118,7 +119,7 @@ def _hptr(a, dtype):
     return ctypes.c_void_p(a.ctypes.data)
 
 
-def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0):
+def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_floor=0.0):
     """tomo_config from the plain-number system description; keeps its arrays alive."""
     n_gs = len(cfg["gs"])
     gs = (tomo_gs * n_gs)()
@@ -131,15 +132,15 @@ def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0):
     tx = (ctypes.c_double * nt)(*[t[0] for t in cfg["targets"]])
     ty = (ctypes.c_double * nt)(*[t[1] for t in cfg["targets"]])
     c = tomo_config(cfg["D"], cfg["obstruction"], cfg["n"], n_gs, gs, nl, lh, lf, cfg["r0"], cfg["L0"],
-                    nt, tx, ty, fft_P, fft_Pcos, max_batch)
+                    nt, tx, ty, fft_P, fft_Pcos, max_batch, int(bool(precond)), float(precond_floor))
     c._keep = (gs, lh, lf, tx, ty)
     return c
 
 
-def tomo_create(cfg, stream=None, max_batch=1, fft_P=0, fft_Pcos=0):
+def tomo_create(cfg, stream=None, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_floor=0.0):
     """Creates a handle; ``stream`` is a torch.cuda.Stream or None (legacy default)."""
     L = lib()
-    c = make_config(cfg, max_batch, fft_P, fft_Pcos)
+    c = make_config(cfg, max_batch, fft_P, fft_Pcos, precond, precond_floor)
     h = ctypes.c_void_p()
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
     _check("tomo_create", L.tomo_create(ctypes.byref(c), s, ctypes.byref(h)))
@@ -171,8 +172,8 @@ def tomo_apply_cos(h, zeta, phase, batch):
     _check("tomo_apply_cos", lib().tomo_apply_cos(h, _dptr(zeta, torch.float32), _dptr(phase, torch.float32), batch))
 
 
-def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=False, check_every=32):
-    return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every)
+def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=False, check_every=32, precond=False):
+    return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every, int(bool(precond)))
 
 
 def tomo_solve(h, slopes, batch, opts, zeta, phase=None):

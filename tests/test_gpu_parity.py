@@ -184,6 +184,25 @@ def test_solve_golden(T, name):
         assert max(rms4) <= 0.5, rms4
 
 
+@pytest.mark.parametrize("name", ["ngs8m", "lgs_mid"])
+def test_pcg_golden(T, name):
+    # the block-circulant preconditioner changes the path, not the solution:
+    # the same bounds as plain CG hold, in fewer iterations
+    g = golden(name)
+    with Handle(T, g["cfg"], max_batch=4, precond=True) as H:
+        z, phi, info = H.solve(g["s"], tol=1e-5, max_iter=20000, max_refine=3, precond=True)
+        zc, _, infoc = H.solve(g["s"], tol=1e-5, max_iter=20000, max_refine=3)
+        print(name, "PCG", info, "CG iters", infoc["iters"])
+        assert (info["status"] == 0).all() and (info["relres"] <= 1e-5).all()
+        err = np.linalg.norm(z - g["zeta"], axis=1)
+        bound = info["relres"] * np.linalg.norm(g["s"], axis=1) / min(g["noise_sigma"]) ** 2
+        assert (err <= bound).all()
+        ref = solve.remove_piston(g["phi_interp"].T).T
+        rms = [NM_PER_RAD * np.sqrt(np.mean((solve.remove_piston(phi[f, 0]) - ref[f]) ** 2)) for f in range(4)]
+        assert max(rms) <= 0.1, rms
+        assert info["iters"].mean() < infoc["iters"].mean()
+
+
 def test_solve_zero_slopes(T):
     cfg = small_cfg(n=6, lgs=True)
     with Handle(T, cfg, max_batch=2) as H:
@@ -239,10 +258,12 @@ def test_elt_css_sampled_rows(T, elt):
         assert np.abs(y[:, rows] - ref).max() <= 1e-5 * scale
 
 
-def test_elt_solve_sampled_residual(T, elt):
+@pytest.mark.parametrize("pcg", [False, True])
+def test_elt_solve_sampled_residual(T, elt, pcg):
     cfg, s = elt
-    with Handle(T, cfg, max_batch=8) as H:
-        z, phi, info = H.solve(s, tol=1e-4)
+    with Handle(T, cfg, max_batch=8, precond=pcg) as H:
+        z, phi, info = H.solve(s, tol=1e-4, precond=pcg)
+        print("ELT", "PCG" if pcg else "CG", info)
         assert (info["status"] == 0).all() and (info["relres"] <= 1e-4).all()
         rows = np.random.default_rng(11).choice(H.info.N, 16, replace=False)
         Arows = cov.css_rows(cfg, rows)
