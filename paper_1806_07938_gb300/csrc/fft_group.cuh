@@ -104,9 +104,12 @@ template <typename C, bool FWD> struct Dft<C, 16, FWD> {
     __device__ __forceinline__ static void run(C* v) { dft_composite<C, 4, 4, FWD>(v); }
 };
 
-// One in-place Stockham stage over G sequences at base + g * gstride.
-template <typename C, int P, int G, int Ns, int R, bool FWD>
-__device__ __forceinline__ void gstage(C* base, int gstride, const C* __restrict__ tw, int lane) {
+// One in-place Stockham stage over G sequences at base + g * gstride.  In the
+// first stage (Ns = 1) only inputs with index < nin are read (the rest are
+// known zeros: the transforms here zero-pad an n-point grid to P); in the last
+// stage (LAST) only outputs with index < nout are written back.
+template <typename C, int P, int G, int Ns, int R, bool FWD, bool LAST>
+__device__ __forceinline__ void gstage(C* base, int gstride, const C* __restrict__ tw, int lane, int nin, int nout) {
     constexpr int PR = P / R;
     constexpr int TT = G * PR;
     constexpr int RD = (TT + 31) / 32;
@@ -119,7 +122,10 @@ __device__ __forceinline__ void gstage(C* base, int gstride, const C* __restrict
             const int g = t / PR, j = t - g * PR, k = j % Ns;
             const C* b = base + g * gstride;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[rd][r] = b[j + r * PR];
+            for (int r = 0; r < R; ++r) {
+                if (Ns == 1) v[rd][r] = j + r * PR < nin ? b[j + r * PR] : cmk<C>(0, 0);
+                else v[rd][r] = b[j + r * PR];
+            }
             if (Ns > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
@@ -137,9 +143,11 @@ __device__ __forceinline__ void gstage(C* base, int gstride, const C* __restrict
         const int t = lane + 32 * rd;
         if (t < TT) {
             const int g = t / PR, j = t - g * PR, k = j % Ns;
-            C* b = base + g * gstride + (j / Ns) * Ns * R + k;
+            const int o = (j / Ns) * Ns * R + k;
+            C* b = base + g * gstride + o;
 #pragma unroll
-            for (int r = 0; r < R; ++r) b[r * Ns] = v[rd][r];
+            for (int r = 0; r < R; ++r)
+                if (!LAST || o + r * Ns < nout) b[r * Ns] = v[rd][r];
         }
     }
     __syncwarp();
@@ -147,12 +155,12 @@ __device__ __forceinline__ void gstage(C* base, int gstride, const C* __restrict
 
 template <typename C, int P, int G, int Ns, bool FWD, int... Rs> struct GStages;
 template <typename C, int P, int G, int Ns, bool FWD> struct GStages<C, P, G, Ns, FWD> {
-    __device__ __forceinline__ static void run(C*, int, const C*, int) {}
+    __device__ __forceinline__ static void run(C*, int, const C*, int, int, int) {}
 };
 template <typename C, int P, int G, int Ns, bool FWD, int R, int... Rest> struct GStages<C, P, G, Ns, FWD, R, Rest...> {
-    __device__ __forceinline__ static void run(C* base, int gstride, const C* tw, int lane) {
-        gstage<C, P, G, Ns, R, FWD>(base, gstride, tw, lane);
-        GStages<C, P, G, Ns * R, FWD, Rest...>::run(base, gstride, tw, lane);
+    __device__ __forceinline__ static void run(C* base, int gstride, const C* tw, int lane, int nin, int nout) {
+        gstage<C, P, G, Ns, R, FWD, sizeof...(Rest) == 0>(base, gstride, tw, lane, nin, nout);
+        GStages<C, P, G, Ns * R, FWD, Rest...>::run(base, gstride, tw, lane, nin, nout);
     }
 };
 
@@ -168,8 +176,9 @@ template <int P> struct Fused { static constexpr bool ok = false; };
     template <> struct Fused<P_> {                                                            \
         static constexpr bool ok = true;                                                      \
         template <typename C, bool FWD>                                                       \
-        __device__ __forceinline__ static void run(C* base, int gstride, const C* tw, int lane) { \
-            GStages<C, P_, kFftGroup, 1, FWD, __VA_ARGS__>::run(base, gstride, tw, lane);     \
+        __device__ __forceinline__ static void run(C* base, int gstride, const C* tw, int lane, int nin, \
+                                                   int nout) {                                \
+            GStages<C, P_, kFftGroup, 1, FWD, __VA_ARGS__>::run(base, gstride, tw, lane, nin, nout); \
         }                                                                                     \
     };
 #ifndef TOMO_PLAN_150_ID
@@ -212,13 +221,16 @@ TOMO_FUSED(32, 4, 8)
 inline bool has_fused_plan(int P) { return P == 150 || P == 180 || P == 160 || P == 40 || P == 32; }
 
 // Transforms kFftGroup sequences base[g * gstride + 0..P) in place with one
-// warp; PC is the compile-time size (0: generic, through scratch[0..P)).  The
-// warp must be converged and the data visible on entry; ends with __syncwarp().
+// warp; PC is the compile-time size (0: generic, through scratch[0..P)).  Only
+// the first nin inputs may be non-zero (the others are not read) and only the
+// first nout outputs are needed (the others may be left unwritten) -- the
+// generic path reads and writes everything.  The warp must be converged and
+// the data visible on entry; ends with __syncwarp().
 template <int PC, typename C, bool FWD>
 __device__ __forceinline__ void fft_g(C* base, int gstride, int count, const FftPlan& pl, const C* tw, C* scratch,
-                                      int lane) {
+                                      int lane, int nin, int nout) {
     if constexpr (Fused<PC>::ok) {
-        Fused<PC>::template run<C, FWD>(base, gstride, tw, lane);
+        Fused<PC>::template run<C, FWD>(base, gstride, tw, lane, nin, nout);
     } else {
         for (int gi = 0; gi < kFftGroup && gi < count; ++gi)
             fft_warp<C>(base + gi * gstride, scratch, pl, tw, FWD, lane, 32);

@@ -130,7 +130,8 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
         }
     }
     __syncthreads();
-    for (int gi = warp; gi < ngrp; gi += kWarps) fft_g<PC, C, true>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane);
+    for (int gi = warp; gi < ngrp; gi += kWarps)
+        fft_g<PC, C, true>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane, n, P);
     if (cgm) {
         const double t = block_sum<T>(rr, red);
         if (threadIdx.x == 0) cg.rr_part[(size_t)f * g.NPin + q] = t;
@@ -291,7 +292,7 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
             const int fl = t / gpf, q0 = (t % gpf) * G;
             if (!act[fl]) continue;
             C* base = D + ((size_t)fl * NPmax + q0) * P;
-            fft_g<PC, C, true>(base, P, G, g.plan, tw, scr + warp * P, lane);
+            fft_g<PC, C, true>(base, P, G, g.plan, tw, scr + warp * P, lane, n, P);
         }
     }
     __syncthreads();
@@ -308,7 +309,7 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
             const int fl = t / gpf, p0 = (t % gpf) * G;
             if (!act[fl]) continue;
             C* base = D + ((size_t)fl * NPmax + p0) * P;
-            fft_g<PC, C, false>(base, P, NPout - p0, g.plan, tw, scr + warp * P, lane);
+            fft_g<PC, C, false>(base, P, NPout - p0, g.plan, tw, scr + warp * P, lane, P, m);
         }
     }
     __syncthreads();
@@ -327,7 +328,10 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
     NPmax += NPmax & 1;
     const size_t fixed = sizeof(C) * (size_t)g.plan.P * (1 + (has_fused_plan(g.plan.P) ? 0 : kWarps));
     const size_t per_frame = sizeof(C) * (size_t)NPmax * g.plan.P;
-    const size_t budget = 72 * 1024;
+#ifndef TOMO_COLS_BUDGET_KB
+#define TOMO_COLS_BUDGET_KB 72
+#endif
+    const size_t budget = TOMO_COLS_BUDGET_KB * 1024;   // shared memory per block of the column pass
     int Bc = (int)((budget > fixed ? budget - fixed : 0) / per_frame);
     if (Bc < 1) Bc = 1;
     if (Bc > kMaxFramesPerBlock) Bc = kMaxFramesPerBlock;
@@ -406,7 +410,8 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
         for (int i = threadIdx.x; i < (ngrp * G - npair) * RS; i += blockDim.x) F[npair * RS + i] = cmk<C>(0, 0);
     load_row_pairs<C>(Y1T + ((size_t)f * g.NPout + pp) * nh * m, m, P, nh, RS, F);
     __syncthreads();
-    for (int gi = warp; gi < ngrp; gi += kWarps) fft_g<PC, C, false>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane);
+    for (int gi = warp; gi < ngrp; gi += kWarps)
+        fft_g<PC, C, false>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane, P, m);
     __syncthreads();
     // gather the valid outputs (W_s), add the noise term, CG dot products
     const size_t vbase = ((size_t)f * g.NPout + pp) * mt.n_vs;
@@ -479,7 +484,7 @@ k_rows_inv_dense(MvmGeom g, const cplx_t<T>* __restrict__ Y1T, T* __restrict__ Y
             else for (int k = lane; k < P; k += 32) wb[gi * P + k] = cmk<C>(0, 0);
         }
         __syncwarp();
-        fft_g<PC, C, false>(wb, P, G, g.plan, tw, wb + G * P, lane);
+        fft_g<PC, C, false>(wb, P, G, g.plan, tw, wb + G * P, lane, P, m);
         for (int gi = 0; gi < G; ++gi) {
             const int r = r0 + 2 * gi;
             if (r >= m) break;
