@@ -158,6 +158,25 @@ tomo_status tomo_layout(const tomo_handle* h, tomo_layout_info* info,
  * x_dev, y_dev: device [batch][N] floats, must not alias. */
 tomo_status tomo_apply_css(tomo_handle* h, const float* x_dev, float* y_dev, int batch);
 
+/* Allocation-free variant of tomo_apply_css (no counterpart in the paper).
+ * For callers that must not allocate device memory once they are running: a
+ * real-time reconstruction loop with a fixed frame deadline (cudaMalloc and
+ * cudaFree synchronise the device and can take milliseconds), or a process
+ * whose device memory is already handed out to another allocator.  The handle
+ * is created beforehand (tomo_create allocates); this call itself allocates
+ * nothing: the two intermediate half spectra of the product live in a 16 MiB
+ * static device buffer of the library, which every GPU that loads the library
+ * keeps until the process exits.  Frames are processed in chunks that fit the
+ * buffer; TOMO_ERANGE if a single frame does not fit (2 * 2nGS * (P/2+1) * n
+ * complex floats must be <= 16 MiB; the 74 x 74, 6-star system needs 1.08 MB).
+ * Same arguments, result and stream as tomo_apply_css.  The first call on a
+ * device looks up the buffer's device address, so make it before any stream
+ * capture.  All calls share the buffer and leave their intermediates in it
+ * (nothing in it needs to start at zero: each call writes every element it
+ * reads); calls that overlap on the GPU, on different streams or handles,
+ * race on it. */
+tomo_status tomo_apply_css_noalloc(tomo_handle* h, const float* x_dev, float* y_dev, int batch);
+
 /* The same operator with FP64 vectors, FFTs and spectra (used for the true
  * residual of the solver). */
 tomo_status tomo_apply_css_f64(tomo_handle* h, const double* x_dev, double* y_dev, int batch);

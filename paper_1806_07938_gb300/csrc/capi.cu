@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -670,9 +671,78 @@ tomo_solve_opts default_opts() {
     return o;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free Sigma_ss product (tomo_apply_css_noalloc).
+// ---------------------------------------------------------------------------
+// Room for the two half-spectrum intermediates of the product (the row-pass
+// output and the column-pass output, NP * (P/2+1) * n complex floats each per
+// frame).  It is a static device array: every GPU that loads this library
+// holds these 16 MiB until the process exits, and every call of the entry
+// point shares them.
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Host code may not use g_noalloc_scratch as a device address (on the host it
+// is only a stand-in symbol); the device address is looked up once per device
+// with that device current.
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDevice {
+    std::once_flag once;
+    void* ptr = nullptr;
+    cudaError_t err = cudaSuccess;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+tomo_status noalloc_scratch(void** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        std::fprintf(stderr, "tomo_apply_css_noalloc: device %d beyond the %d supported\n", dev, kNoAllocMaxDevices);
+        return TOMO_ERANGE;
+    }
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    std::call_once(d.once, [&d] { d.err = cudaGetSymbolAddress(&d.ptr, g_noalloc_scratch); });
+    if (d.err != cudaSuccess || d.ptr == nullptr) {
+        std::fprintf(stderr, "tomo_apply_css_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(d.err));
+        return TOMO_ECUDA;
+    }
+    *out = d.ptr;
+    return TOMO_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+tomo_status tomo_apply_css_noalloc(tomo_handle* h, const float* x, float* y, int batch) {
+    if (!h || !x || !y || batch < 0 || x == y) return TOMO_EINVAL;
+    const size_t half = (size_t)h->NP * (h->P / 2 + 1) * h->n * sizeof(float2);
+    const size_t per_frame = 2 * half;
+    if (per_frame > kNoAllocScratchBytes) {
+        std::fprintf(stderr,
+                     "tomo_apply_css_noalloc: one frame needs %zu bytes of scratch, more than the %zu bytes of the "
+                     "static buffer (use tomo_apply_css)\n",
+                     per_frame, kNoAllocScratchBytes);
+        return TOMO_ERANGE;
+    }
+    void* scratch = nullptr;
+    TRY(noalloc_scratch(&scratch));
+    const int chunk = (int)std::min<size_t>(kNoAllocScratchBytes / per_frame, (size_t)1 << 20);
+    float2* X1 = static_cast<float2*>(scratch);
+    float2* Y1 = X1 + (size_t)chunk * (half / sizeof(float2));
+    Launch L = launch_of(h);
+    for (int f0 = 0; f0 < batch; f0 += chunk) {
+        const int B = std::min(chunk, batch - f0);
+        const float* xb = x + (size_t)f0 * h->N;
+        float* yb = y + (size_t)f0 * h->N;
+        CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, xb, nullptr, nullptr, X1, h->d_tw32)));
+        CK((cols_mul<float>(L, h->g_ss, B, nullptr, X1, Y1, h->d_K32, h->d_tw32)));
+        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, nullptr, Y1, xb, h->d_noise_var, yb, nullptr,
+                                          h->d_tw32)));
+    }
+    return TOMO_OK;
+}
+
 
 tomo_status tomo_create(const tomo_config* cfg, void* cuda_stream, tomo_handle** out) {
     if (!out) return TOMO_EINVAL;

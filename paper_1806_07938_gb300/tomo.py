@@ -53,7 +53,8 @@ class tomo_frame_info(ctypes.Structure):
 FRAME_INFO_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("status", np.int32),
                              ("pad_", np.int32), ("relres", np.float64)])
 
-EXPORTS = ("tomo_create", "tomo_layout", "tomo_apply_css", "tomo_apply_css_f64", "tomo_apply_cos",
+EXPORTS = ("tomo_create", "tomo_layout", "tomo_apply_css", "tomo_apply_css_noalloc", "tomo_apply_css_f64",
+           "tomo_apply_cos",
            "tomo_solve", "tomo_solve_host", "tomo_launch_count", "tomo_set_kernel_timing",
            "tomo_get_kernel_timing", "tomo_destroy", "tomo_strerror")
 KERNEL_NAMES = ("rows_fwd", "cols_mul", "rows_inv", "cg_scalars")
@@ -81,6 +82,7 @@ def lib(path=None):
     L.tomo_create.argtypes = [ctypes.POINTER(tomo_config), vp, ctypes.POINTER(vp)]
     L.tomo_layout.argtypes = [vp, ctypes.POINTER(tomo_layout_info), vp, vp]
     L.tomo_apply_css.argtypes = [vp, vp, vp, i]
+    L.tomo_apply_css_noalloc.argtypes = [vp, vp, vp, i]
     L.tomo_apply_css_f64.argtypes = [vp, vp, vp, i]
     L.tomo_apply_cos.argtypes = [vp, vp, vp, i]
     L.tomo_solve.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
@@ -160,6 +162,13 @@ def tomo_layout(h):
 def tomo_apply_css(h, x, y, batch):
     import torch
     _check("tomo_apply_css", lib().tomo_apply_css(h, _dptr(x, torch.float32), _dptr(y, torch.float32), batch))
+
+
+def tomo_apply_css_noalloc(h, x, y, batch):
+    """tomo_apply_css without any device allocation (intermediates in the library's static buffer)."""
+    import torch
+    _check("tomo_apply_css_noalloc",
+           lib().tomo_apply_css_noalloc(h, _dptr(x, torch.float32), _dptr(y, torch.float32), batch))
 
 
 def tomo_apply_css_f64(h, x, y, batch):
