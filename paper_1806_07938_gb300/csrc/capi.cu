@@ -164,7 +164,7 @@ Launch launch_of(tomo_handle* h) { return Launch{h->stream, &h->launches}; }
 tomo_status apply_ss32(tomo_handle* h, const Launch& L, const float* x, float* y, int B, const FrameState* st,
                        const CgVecs* cg) {
     CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, x, cg, st, h->X1, h->d_tw32)));
-    CK((cols_mul<float>(L, h->g_ss, B, st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
+    CK((cols_mul<float>(L, h->g_ss, B, st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
     const float* xin = cg ? cg->p : x;
     float* yout = cg ? cg->Ap : y;
     CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, st, h->Y1, xin, h->d_noise_var, yout, cg, h->d_tw32)));
@@ -177,7 +177,7 @@ CgVecs cg_vecs(tomo_handle* h, int mode, double* dots) {
 
 tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double* y, int B) {
     CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1d, h->d_tw64)));
-    CK((cols_mul<double>(L, h->g_ss, B, nullptr, h->X1d, h->Y1d, h->d_K64, h->d_tw64)));
+    CK((cols_mul<double>(L, h->g_ss, B, nullptr, h->X1d, h->Y1d, h->d_K64, h->d_tw64, false)));
     CK((rows_inv_masked<double, double>(L, h->g_ss, h->mt, B, nullptr, h->Y1d, x, h->d_noise_var, y, nullptr,
                                         h->d_tw64)));
     return TOMO_OK;
@@ -187,7 +187,7 @@ tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi
     CK((rows_fwd<float, float>(L, h->g_os, h->mt, B, z, nullptr, nullptr, h->Xc, h->d_twc32)));
     const size_t kc_stride = (size_t)h->g_os.nh * h->Pc * h->cos_layers * h->NP;
     for (int t = 0; t < h->n_targets; ++t) {
-        CK((cols_mul<float>(L, h->g_os, B, nullptr, h->Xc, h->Yc, h->d_Kc32 + t * kc_stride, h->d_twc32)));
+        CK((cols_mul<float>(L, h->g_os, B, nullptr, h->Xc, h->Yc, h->d_Kc32 + t * kc_stride, h->d_twc32, false)));
         CK((rows_inv_dense<float>(L, h->g_os, B, h->Yc, h->Ydc, h->d_twc32)));
         CK(interp(L, B, h->n_targets, t, h->cos_layers, h->m, h->n_vphi, h->Ydc, h->d_iidx, h->d_iw, phi));
     }
@@ -222,7 +222,7 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, bool pcg, std::vec
         const CgVecs cg = cg_vecs(h, 1, h->dot_part);
         CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32)));
         TRY(mark(0));
-        CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
+        CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
         TRY(mark(1));
         CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->Ap, &cg,
                                           h->d_tw32)));
@@ -235,14 +235,14 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, bool pcg, std::vec
     const CgVecs cgA = cg_vecs(h, 2, h->dot_part);
     CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cgM, h->st, h->X1, h->d_tw32)));
     TRY(mark(0));
-    CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_M32, h->d_tw32)));
+    CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_M32, h->d_tw32, true)));
     TRY(mark(1));
     CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->r, h->d_zero_var, h->z, &cgM,
                                       h->d_tw32)));
     TRY(mark(2));
     CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, h->z, nullptr, h->st, h->X1, h->d_tw32)));
     TRY(mark(0));
-    CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32)));
+    CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
     TRY(mark(1));
     CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->z, h->d_noise_var, h->w, &cgA,
                                       h->d_tw32)));
@@ -452,14 +452,18 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         double2* H = nullptr;
         CK(cudaMalloc(&G, sizeof(double) * Gsz));
         CK(cudaMalloc(&H, sizeof(double2) * (size_t)npl * (h->P / 2 + 1) * h->P));
+        float2* Kfull = nullptr;
+        CK(cudaMalloc(&Kfull, sizeof(float2) * (size_t)npl * (h->P / 2 + 1) * h->P));
         TRY(dalloc(h, &h->d_K64, (size_t)npl * (h->P / 2 + 1) * h->P));
-        TRY(dalloc(h, &h->d_K32, (size_t)npl * (h->P / 2 + 1) * h->P));
+        TRY(dalloc(h, &h->d_K32, (size_t)(h->NP * (h->NP + 1) / 2) * (h->P / 2 + 1) * h->P));
         CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
         CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G, false));
-        CK(spectra(L, h->P, npl, h->NP, h->plan, G, H, h->d_tw64, h->d_K64, h->d_K32));
+        CK(spectra(L, h->P, npl, h->NP, h->plan, G, H, h->d_tw64, h->d_K64, Kfull));
+        CK(pack_hermitian(L, h->P, h->NP, Kfull, h->d_K32));
         CK(cudaStreamSynchronize(h->stream));
         cudaFree(G);
         cudaFree(H);
+        cudaFree(Kfull);
     }
     // --- block-circulant preconditioner on the same P x P torus ------------------------
     if (c->precond) {
@@ -471,18 +475,22 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         CK(cudaMalloc(&G, sizeof(double) * Gsz));
         CK(cudaMalloc(&H, sizeof(double2) * Ksz));
         CK(cudaMalloc(&K64, sizeof(double2) * Ksz));
-        TRY(dalloc(h, &h->d_M32, Ksz));
+        float2* Mfull = nullptr;
+        CK(cudaMalloc(&Mfull, sizeof(float2) * Ksz));
+        TRY(dalloc(h, &h->d_M32, (size_t)(h->NP * (h->NP + 1) / 2) * (h->P / 2 + 1) * h->P));
         TRY(dalloc(h, &h->d_zero_var, h->NP));
         CK(cudaMemsetAsync(h->d_zero_var, 0, sizeof(double) * h->NP, h->stream));
         CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
         CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G, true));
         CK(spectra(L, h->P, npl, h->NP, h->plan, G, H, h->d_tw64, K64, nullptr));
         const double floor_c = c->precond_floor > 0 ? c->precond_floor : 3.0;
-        CK(precond_spectra(L, h->P, h->NP, K64, h->d_noise_var, floor_c, h->d_M32));
+        CK(precond_spectra(L, h->P, h->NP, K64, h->d_noise_var, floor_c, Mfull));
+        CK(pack_hermitian(L, h->P, h->NP, Mfull, h->d_M32));
         CK(cudaStreamSynchronize(h->stream));
         cudaFree(G);
         cudaFree(H);
         cudaFree(K64);
+        cudaFree(Mfull);
     }
     // --- Sigma_phi_s generators and spectra, one set per target ------------------------
     {
@@ -736,7 +744,7 @@ tomo_status tomo_apply_css_noalloc(tomo_handle* h, const float* x, float* y, int
         const float* xb = x + (size_t)f0 * h->N;
         float* yb = y + (size_t)f0 * h->N;
         CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, xb, nullptr, nullptr, X1, h->d_tw32)));
-        CK((cols_mul<float>(L, h->g_ss, B, nullptr, X1, Y1, h->d_K32, h->d_tw32)));
+        CK((cols_mul<float>(L, h->g_ss, B, nullptr, X1, Y1, h->d_K32, h->d_tw32, true)));
         CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, nullptr, Y1, xb, h->d_noise_var, yb, nullptr,
                                           h->d_tw32)));
     }

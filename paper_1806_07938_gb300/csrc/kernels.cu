@@ -225,6 +225,58 @@ __device__ __forceinline__ void block_mul(C* D, int NPmax, int P, int nf, const 
     }
 }
 
+// Hermitian variant for Sigma_ss (NP x NP blocks with K_qp = conj K_pq): only
+// the upper triangle is stored, [kx][ky][e] with e(p, q) the row-major index of
+// p <= q.  Each round stages its ky range of packed entries in shared memory
+// (one coalesced copy), and thread (ky, p) assembles its row K_p. from it.
+__host__ __device__ constexpr int herm_index(int NP, int p, int q) { return p * NP - p * (p - 1) / 2 + (q - p); }
+
+template <typename C, int NP>
+__device__ __forceinline__ void block_mul_herm(C* D, int NPmax, int P, int nf, const int* act, const C* __restrict__ Kc,
+                                               C* Ks) {
+    using T = decltype(C::x);
+    constexpr int NE = NP * (NP + 1) / 2;
+    const int kyr = blockDim.x / NP;
+    const int kyl = threadIdx.x / NP, pp = threadIdx.x % NP;
+    for (int ky0 = 0; ky0 < P; ky0 += kyr) {
+        const int nky = min(kyr, P - ky0);
+        for (int i = threadIdx.x; i < nky * NE; i += blockDim.x) Ks[i] = __ldg(&Kc[(size_t)ky0 * NE + i]);
+        __syncthreads();
+        const int ky = ky0 + kyl;
+        const bool on = kyl < nky;
+        C y[kMaxFramesPerBlock];
+        if (on) {
+            C k[NP];
+            const C* Kr = Ks + kyl * NE;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) k[q] = q >= pp ? Kr[herm_index(NP, pp, q)] : cconj(Kr[herm_index(NP, q, pp)]);
+#pragma unroll
+            for (int fl = 0; fl < kMaxFramesPerBlock; ++fl) {
+                if (fl < nf && act[fl]) {
+                    const C* col = D + (size_t)fl * NPmax * P + ky;
+                    T ar = 0, ai = 0;
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        const C x = col[q * P];
+                        ar = fma(k[q].x, x.x, ar);
+                        ar = fma(-k[q].y, x.y, ar);
+                        ai = fma(k[q].x, x.y, ai);
+                        ai = fma(k[q].y, x.x, ai);
+                    }
+                    y[fl] = cmk<C>(ar, ai);
+                }
+            }
+        }
+        __syncthreads();
+        if (on) {
+#pragma unroll
+            for (int fl = 0; fl < kMaxFramesPerBlock; ++fl)
+                if (fl < nf && act[fl]) D[((size_t)fl * NPmax + pp) * P + ky] = y[fl];
+        }
+        __syncthreads();
+    }
+}
+
 template <typename C>
 __device__ void block_mul_rt(C* D, int NPmax, int P, int nf, const int* act, const C* __restrict__ Kc, int NPin,
                              int NPout) {
@@ -260,7 +312,8 @@ __device__ void block_mul_rt(C* D, int NPmax, int P, int nf, const int* act, con
 template <typename T, int PC>
 __global__ void __launch_bounds__(kThreads, TOMO_MIN_BLOCKS)
 k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __restrict__ X1T,
-           cplx_t<T>* __restrict__ Y1T, const cplx_t<T>* __restrict__ K, const cplx_t<T>* __restrict__ twg) {
+           cplx_t<T>* __restrict__ Y1T, const cplx_t<T>* __restrict__ K, const cplx_t<T>* __restrict__ twg,
+           int herm) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = g.plan.P, n = g.n, m = g.m, nh = g.nh, NPin = g.NPin, NPout = g.NPout;
@@ -270,6 +323,7 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* scr = tw + P;
     C* D = scr + (Fused<PC>::ok ? 0 : kWarps * P); // [Bc][NPmax][P]
+    C* Ks = D + (size_t)Bc * NPmax * P;            // packed K of one round (Hermitian path)
     __shared__ int act[kMaxFramesPerBlock];
     const int kx = blockIdx.x;
     const int f0 = blockIdx.y * Bc;
@@ -278,12 +332,16 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) act[i] = st ? st[f0 + i].active : 1;
     __syncthreads();
-    // load the columns (rows >= n are the zero padding)
-    for (int i = threadIdx.x; i < nf * NPin * P; i += blockDim.x) {
-        const int r = i % P, t = i / P, q = t % NPin, fl = t / NPin;
-        C v = cmk<C>(0, 0);
-        if (r < n && act[fl]) v = X1T[(((size_t)(f0 + fl) * NPin + q) * nh + kx) * n + r];
-        D[((size_t)fl * NPmax + q) * P + r] = v;
+    // load the columns, one warp per (frame, plane); rows >= n are the zero
+    // padding, which the pruned forward transform never reads
+    for (int t = warp; t < nf * NPin; t += kWarps) {
+        const int fl = t / NPin, q = t - fl * NPin;
+        if (!act[fl]) continue;
+        const C* src = X1T + (((size_t)(f0 + fl) * NPin + q) * nh + kx) * n;
+        C* dst = D + ((size_t)fl * NPmax + q) * P;
+        for (int r = lane; r < n; r += 32) dst[r] = src[r];
+        if (!Fused<PC>::ok)
+            for (int r = n + lane; r < P; r += 32) dst[r] = cmk<C>(0, 0);
     }
     __syncthreads();
     {
@@ -298,7 +356,19 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     __syncthreads();
     // block multiply: one thread per (ky, p), frames looped
     const C* Kc = K + (size_t)kx * NPin * P * NPout;
-    if (NPin == 12 && NPout == 12) block_mul<C, 12, 12>(D, NPmax, P, nf, act, Kc);
+    const C* Kh = K + (size_t)kx * P * (NPin * (NPin + 1) / 2);
+    if (herm) {
+        switch (NPin) {
+            case 2: block_mul_herm<C, 2>(D, NPmax, P, nf, act, Kh, Ks); break;
+            case 4: block_mul_herm<C, 4>(D, NPmax, P, nf, act, Kh, Ks); break;
+            case 6: block_mul_herm<C, 6>(D, NPmax, P, nf, act, Kh, Ks); break;
+            case 8: block_mul_herm<C, 8>(D, NPmax, P, nf, act, Kh, Ks); break;
+            case 10: block_mul_herm<C, 10>(D, NPmax, P, nf, act, Kh, Ks); break;
+            case 12: block_mul_herm<C, 12>(D, NPmax, P, nf, act, Kh, Ks); break;
+            case 14: block_mul_herm<C, 14>(D, NPmax, P, nf, act, Kh, Ks); break;
+            default: block_mul_herm<C, 16>(D, NPmax, P, nf, act, Kh, Ks); break;
+        }
+    } else if (NPin == 12 && NPout == 12) block_mul<C, 12, 12>(D, NPmax, P, nf, act, Kc);
     else if (NPin == 6 && NPout == 6) block_mul<C, 6, 6>(D, NPmax, P, nf, act, Kc);
     else if (NPin == 4 && NPout == 4) block_mul<C, 4, 4>(D, NPmax, P, nf, act, Kc);
     else if (NPin == 2 && NPout == 2) block_mul<C, 2, 2>(D, NPmax, P, nf, act, Kc);
@@ -313,20 +383,25 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nf * NPout * m; i += blockDim.x) {
-        const int r = i % m, t = i / m, pp = t % NPout, fl = t / NPout;
-        if (act[fl]) Y1T[(((size_t)(f0 + fl) * NPout + pp) * nh + kx) * m + r] = D[((size_t)fl * NPmax + pp) * P + r];
+    for (int t = warp; t < nf * NPout; t += kWarps) {
+        const int fl = t / NPout, pp = t - fl * NPout;
+        if (!act[fl]) continue;
+        const C* src = D + ((size_t)fl * NPmax + pp) * P;
+        C* dst = Y1T + (((size_t)(f0 + fl) * NPout + pp) * nh + kx) * m;
+        for (int r = lane; r < m; r += 32) dst[r] = src[r];
     }
 }
 
 template <typename T>
 cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState* st, const cplx_t<T>* X1T,
-                     cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw) {
+                     cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw, bool herm) {
     using C = cplx_t<T>;
     if (g.NPin > 16) return cudaErrorInvalidValue;
     int NPmax = g.NPin > g.NPout ? g.NPin : g.NPout;
     NPmax += NPmax & 1;
-    const size_t fixed = sizeof(C) * (size_t)g.plan.P * (1 + (has_fused_plan(g.plan.P) ? 0 : kWarps));
+    if (herm && (g.NPin != g.NPout || (g.NPin & 1) || g.NPin < 2 || g.NPin > 16)) return cudaErrorInvalidValue;
+    const size_t ks = herm ? sizeof(C) * (size_t)(kThreads / g.NPin) * (g.NPin * (g.NPin + 1) / 2) : 0;
+    const size_t fixed = sizeof(C) * (size_t)g.plan.P * (1 + (has_fused_plan(g.plan.P) ? 0 : kWarps)) + ks;
     const size_t per_frame = sizeof(C) * (size_t)NPmax * g.plan.P;
 #ifndef TOMO_COLS_BUDGET_KB
 #define TOMO_COLS_BUDGET_KB 72
@@ -339,7 +414,8 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
     const size_t smem = fixed + per_frame * Bc;
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
 #define TOMO_L(PC) \
-    k_cols_mul<T, PC><<<dim3(g.nh, (B + Bc - 1) / Bc), kThreads, smem, L.stream>>>(g, B, Bc, st, X1T, Y1T, K, tw)
+    k_cols_mul<T, PC><<<dim3(g.nh, (B + Bc - 1) / Bc), kThreads, smem, L.stream>>>(g, B, Bc, st, X1T, Y1T, K, tw, \
+                                                                                  (int)herm)
     TOMO_DISPATCH_P(g.plan.P, TOMO_L)
 #undef TOMO_L
     count(L);
@@ -1054,6 +1130,30 @@ cudaError_t precond_spectra(const Launch& L, int P, int NP, const double2* K64, 
     return cudaGetLastError();
 }
 
+// Packs a full NP x NP spectrum [nh][NP(q)][P][NP(p)] into the Hermitian
+// upper-triangle layout [nh][P][e(p <= q)], storing (K_pq + conj K_qp) / 2.
+__global__ void k_pack_hermitian(int P, int NP, const float2* __restrict__ Kf, float2* __restrict__ Kp) {
+    const int nh = P / 2 + 1, NE = NP * (NP + 1) / 2;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)nh * P * NE) return;
+    const int e = (int)(i % NE);
+    const size_t fk = i / NE;
+    const int ky = (int)(fk % P), kx = (int)(fk / P);
+    int p = 0;
+    while (herm_index(NP, p + 1, p + 1) <= e && p + 1 < NP) ++p;
+    const int q = p + (e - herm_index(NP, p, p));
+    const float2 a = Kf[(((size_t)kx * NP + q) * P + ky) * NP + p];
+    const float2 b = Kf[(((size_t)kx * NP + p) * P + ky) * NP + q];
+    Kp[i] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+}
+
+cudaError_t pack_hermitian(const Launch& L, int P, int NP, const float2* Kfull, float2* Kpacked) {
+    const size_t total = (size_t)(P / 2 + 1) * P * (NP * (NP + 1) / 2);
+    k_pack_hermitian<<<(unsigned)((total + 255) / 256), 256, 0, L.stream>>>(P, NP, Kfull, Kpacked);
+    count(L);
+    return cudaGetLastError();
+}
+
 // phi[f][t][v] = sum_k sum_c w[k][v][c] Yd[f][k][idx[k][v][c]]  (Eq. interp, sum over layers)
 __global__ void k_interp(int B, int T_all, int t, int n_layers, int m, int n_vphi, const float* __restrict__ Yd,
                          const int* __restrict__ idx, const float* __restrict__ w, float* __restrict__ phi) {
@@ -1119,9 +1219,9 @@ template cudaError_t rows_fwd<float, float>(const Launch&, const MvmGeom&, const
 template cudaError_t rows_fwd<double, double>(const Launch&, const MvmGeom&, const MaskTables&, int, const double*,
                                               const CgVecs*, const FrameState*, double2*, const double2*);
 template cudaError_t cols_mul<float>(const Launch&, const MvmGeom&, int, const FrameState*, const float2*, float2*,
-                                     const float2*, const float2*);
+                                     const float2*, const float2*, bool);
 template cudaError_t cols_mul<double>(const Launch&, const MvmGeom&, int, const FrameState*, const double2*, double2*,
-                                      const double2*, const double2*);
+                                      const double2*, const double2*, bool);
 template cudaError_t rows_inv_masked<float, float>(const Launch&, const MvmGeom&, const MaskTables&, int,
                                                    const FrameState*, const float2*, const float*, const double*,
                                                    float*, const CgVecs*, const float2*);

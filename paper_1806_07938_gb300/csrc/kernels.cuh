@@ -86,11 +86,14 @@ cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, in
                      cplx_t<T>* X1T, const cplx_t<T>* tw);
 
 // Column pass: forward column FFT of the NPin planes, per-frequency block
-// multiply by K [nh][NPin][P][NPout], inverse column FFT, keep rows < m:
-// X1T [B][NPin][nh][n] -> Y1T [B][NPout][nh][m].
+// multiply by K [nh][NPin][P][NPout] (herm = false) or by the Hermitian
+// upper triangle [nh][P][e(p <= q)] (herm = true, NPin = NPout), inverse
+// column FFT, keep rows < m: X1T [B][NPin][nh][n] -> Y1T [B][NPout][nh][m].
 template <typename T>
 cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState* st,
-                     const cplx_t<T>* X1T, cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw);
+                     const cplx_t<T>* X1T, cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw, bool herm);
+// Full [nh][NP][P][NP] spectrum -> Hermitian upper-triangle layout [nh][P][e].
+cudaError_t pack_hermitian(const Launch& L, int P, int NP, const float2* Kfull, float2* Kpacked);
 
 // Row-inverse pass to masked output (Sigma_ss): y = crop/mask(IFFT rows) +
 // noise_var[plane] * xin.  CG mode (cg != nullptr; xin = cg->p, y = cg->Ap):
