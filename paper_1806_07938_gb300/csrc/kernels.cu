@@ -78,22 +78,29 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
     const size_t vbase = ((size_t)f * g.NPin + q) * mt.n_vs;
     const bool cgm = cg.p != nullptr;
     double rr = 0.0;
+    float* __restrict__ vx = cg.x;
+    float* __restrict__ vr = cg.r;
+    float* __restrict__ vp = cg.p;
+    float* __restrict__ vAp = cg.Ap;
+    const float* __restrict__ vz = cg.z;
+    const float* __restrict__ vw = cg.w;
+    const int* __restrict__ rowcol = mt.rowcol;
     if (cgm && cg.mode == 1) {
         const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
 #pragma unroll 4
         for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
             const size_t i = vbase + e;
-            const int rc = mt.rowcol[e];
-            const float pe = cg.p[i];
-            float re = cg.r[i];
+            const int rc = rowcol[e];
+            const float pe = vp[i];
+            float re = vr[i];
             if (alpha != 0.f) {
-                const float ape = cg.Ap[i];
-                cg.x[i] += alpha * pe;
+                const float ape = vAp[i];
+                vx[i] += alpha * pe;
                 re -= alpha * ape;
-                cg.r[i] = re;
+                vr[i] = re;
             }
             const float pn = re + beta * pe;
-            cg.p[i] = pn;
+            vp[i] = pn;
             rr += (double)re * re;
             const int row = rc >> 16, col = rc & 0xffff;
             T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
@@ -104,17 +111,17 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
 #pragma unroll 4
         for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
             const size_t i = vbase + e;
-            const int rc = mt.rowcol[e];
-            const float pn = cg.z[i] + beta * cg.p[i];
-            const float sn = cg.w[i] + beta * cg.Ap[i];
-            float re = cg.r[i];
+            const int rc = rowcol[e];
+            const float pn = vz[i] + beta * vp[i];
+            const float sn = vw[i] + beta * vAp[i];
+            float re = vr[i];
             if (alpha != 0.f) {
-                cg.x[i] += alpha * pn;
+                vx[i] += alpha * pn;
                 re -= alpha * sn;
-                cg.r[i] = re;
+                vr[i] = re;
             }
-            cg.p[i] = pn;
-            cg.Ap[i] = sn;
+            vp[i] = pn;
+            vAp[i] = sn;
             rr += (double)re * re;
             const int row = rc >> 16, col = rc & 0xffff;
             T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
@@ -123,10 +130,10 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
     } else {
 #pragma unroll 4
         for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
-            const int rc = mt.rowcol[e];
+            const int rc = rowcol[e];
             const int row = rc >> 16, col = rc & 0xffff;
             T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
-            *dst = (T)x[vbase + e];
+            *dst = (T)__ldg(x + vbase + e);
         }
     }
     __syncthreads();
@@ -240,7 +247,19 @@ __device__ __forceinline__ void block_mul_herm(C* D, int NPmax, int P, int nf, c
     const int kyl = threadIdx.x / NP, pp = threadIdx.x % NP;
     for (int ky0 = 0; ky0 < P; ky0 += kyr) {
         const int nky = min(kyr, P - ky0);
-        for (int i = threadIdx.x; i < nky * NE; i += blockDim.x) Ks[i] = __ldg(&Kc[(size_t)ky0 * NE + i]);
+        {
+            const int cnt = nky * NE;
+            const C* src = Kc + (size_t)ky0 * NE;
+            for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * blockDim.x) {
+                C v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u * (int)blockDim.x < cnt) v[u] = __ldg(src + i0 + u * blockDim.x);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u * (int)blockDim.x < cnt) Ks[i0 + u * blockDim.x] = v[u];
+            }
+        }
         __syncthreads();
         const int ky = ky0 + kyl;
         const bool on = kyl < nky;
@@ -333,15 +352,46 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     for (int i = threadIdx.x; i < nf; i += blockDim.x) act[i] = st ? st[f0 + i].active : 1;
     __syncthreads();
     // load the columns, one warp per (frame, plane); rows >= n are the zero
-    // padding, which the pruned forward transform never reads
-    for (int t = warp; t < nf * NPin; t += kWarps) {
-        const int fl = t / NPin, q = t - fl * NPin;
-        if (!act[fl]) continue;
-        const C* src = X1T + (((size_t)(f0 + fl) * NPin + q) * nh + kx) * n;
-        C* dst = D + ((size_t)fl * NPmax + q) * P;
-        for (int r = lane; r < n; r += 32) dst[r] = src[r];
-        if (!Fused<PC>::ok)
-            for (int r = n + lane; r < P; r += 32) dst[r] = cmk<C>(0, 0);
+    // padding, which the pruned forward transform never reads.  All loads of a
+    // warp's two columns are issued before the first store (latency hiding).
+    for (int t0 = warp * 2; t0 < nf * NPin; t0 += kWarps * 2) {
+        C v[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = t0 + u;
+            const int fl = t / NPin, q = t - fl * NPin;
+            const bool ok = t < nf * NPin && act[fl < nf ? fl : 0];
+            const C* src = X1T + (((size_t)(f0 + (ok ? fl : 0)) * NPin + (ok ? q : 0)) * nh + kx) * n;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = lane + 32 * i;
+                if (ok && r < n) v[u][i] = __ldg(src + r);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = t0 + u;
+            const int fl = t / NPin, q = t - fl * NPin;
+            if (t >= nf * NPin || !act[fl]) continue;
+            C* dst = D + ((size_t)fl * NPmax + q) * P;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = lane + 32 * i;
+                if (r < n) dst[r] = v[u][i];
+            }
+            if (!Fused<PC>::ok)
+                for (int r = n + lane; r < P; r += 32) dst[r] = cmk<C>(0, 0);
+        }
+    }
+    // rows beyond 128 (n > 128) are loaded here
+    if (n > 128) {
+        for (int t = warp; t < nf * NPin; t += kWarps) {
+            const int fl = t / NPin, q = t - fl * NPin;
+            if (!act[fl]) continue;
+            const C* src = X1T + (((size_t)(f0 + fl) * NPin + q) * nh + kx) * n;
+            C* dst = D + ((size_t)fl * NPmax + q) * P;
+            for (int r = 128 + lane; r < n; r += 32) dst[r] = src[r];
+        }
     }
     __syncthreads();
     {
@@ -446,18 +496,37 @@ __device__ __forceinline__ void pack_row_pair(const C* S, int m, int r, int P, i
 // extension; DC and Nyquist taken real), so that one inverse complex FFT per
 // pair returns row 2j in .x and row 2j+1 in .y.
 template <typename C>
+__device__ __forceinline__ void put_row_pair(C* F, int RS, int P, int j, int k, C a, C b) {
+    if (k == 0 || 2 * k == P) { a.y = 0; b.y = 0; }
+    F[j * RS + k] = cmk<C>(a.x - b.y, a.y + b.x);
+    if (k != 0 && 2 * k != P) {
+        const C ac = cconj(a), bc = cconj(b);
+        F[j * RS + P - k] = cmk<C>(ac.x - bc.y, ac.y + bc.x);
+    }
+}
+
+template <typename C>
 __device__ __forceinline__ void load_row_pairs(const C* __restrict__ src, int m, int P, int nh, int RS, C* F) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int npair = (m + 1) / 2;
-    for (int k = warp; k < nh; k += kWarps) {
-        for (int j = lane; j < npair; j += 32) {
-            C a = src[(size_t)k * m + 2 * j];
-            C b = 2 * j + 1 < m ? src[(size_t)k * m + 2 * j + 1] : cmk<C>(0, 0);
-            if (k == 0 || 2 * k == P) { a.y = 0; b.y = 0; }
-            F[j * RS + k] = cmk<C>(a.x - b.y, a.y + b.x);
-            if (k != 0 && 2 * k != P) {
-                const C ac = cconj(a), bc = cconj(b);
-                F[j * RS + P - k] = cmk<C>(ac.x - bc.y, ac.y + bc.x);
+    const int total = nh * npair;
+    constexpr int U = 4;
+    for (int i0 = threadIdx.x; i0 < total; i0 += U * blockDim.x) {
+        C a[U], b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < total) {
+                const int k = i / npair, j = i - k * npair;
+                a[u] = __ldg(src + (size_t)k * m + 2 * j);
+                b[u] = 2 * j + 1 < m ? __ldg(src + (size_t)k * m + 2 * j + 1) : cmk<C>(0, 0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < total) {
+                const int k = i / npair, j = i - k * npair;
+                put_row_pair<C>(F, RS, P, j, k, a[u], b[u]);
             }
         }
     }
@@ -493,18 +562,21 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
     const size_t vbase = ((size_t)f * g.NPout + pp) * mt.n_vs;
     const TIn nv = (TIn)noise_var[pp];
     const bool cgm = cg.p != nullptr;
+    const float* __restrict__ vr = cg.r;
+    const int* __restrict__ rowcol = mt.rowcol;
     double acc = 0.0, acc_r = 0.0, acc_a = 0.0;
 #pragma unroll 4
     for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
-        const int rc = mt.rowcol[e];
+        const int rc = rowcol[e];
         const int row = rc >> 16, col = rc & 0xffff;
+        const TIn xi = __ldg(xin + vbase + e);
+        const float ri = cgm ? __ldg(vr + vbase + e) : 0.f;
         const T v = reinterpret_cast<const T*>(F + (row >> 1) * RS + col)[row & 1];
-        const TIn xi = xin[vbase + e];
         const TIn out = (TIn)v + nv * xi;
         y[vbase + e] = out;
         if (cgm) {
             acc += (double)xi * (double)out;
-            acc_r += (double)cg.r[vbase + e] * (double)out;
+            acc_r += (double)ri * (double)out;
             acc_a += (double)out * (double)out;
         }
     }
