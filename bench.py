@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=FRAMES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     return ap.parse_args()
 
 
@@ -219,9 +220,34 @@ def dist_setup(use_cuda):
 def workload(frames, seed):
     from paper_1806_07938_gb300 import workloads as W
     cfg = W.config("elt_ltao")
-    full, sigma = W.slope_frames(cfg, frames, seed=seed)
+    full, sigma = W.slope_frames_parallel(cfg, frames, seed=seed)
     cfg["noise_sigma"] = [float(s) for s in sigma]
     return cfg, full
+
+
+def train_warm_start(tomo, torch, h, cfg, layout, sub, seed, n_train=256, steps=200, B=32):
+    """Offline: seeded training frames, their PCG solutions, Adam on the warm-start network."""
+    import numpy as np
+    from paper_1806_07938_gb300 import workloads as W
+    full, sigma = W.slope_frames_parallel(cfg, n_train, seed=seed)
+    # the reconstructor's noise model is the bench frames'; the training frames only need the same statistics
+    s = torch.tensor(tomo.valid_slopes(full, sub), dtype=torch.float32, device="cuda").contiguous()
+    z = torch.zeros_like(s)
+    opts = tomo.solve_opts(tol=1e-5, max_iter=30000, max_refine=3, precond=True)
+    for b0 in range(0, n_train, 64):
+        nb = min(64, n_train - b0)
+        tomo.tomo_solve(h, s[b0:b0 + nb].contiguous(), nb, opts, z[b0:b0 + nb])
+    NP = 2 * layout.n_gs
+    tomo.tomo_ws_init(h, hidden=32, max_batch=64, in_scale=float(1.0 / s.std().item()),
+                      out_scale=float(z.std().item()))
+    tomo.tomo_ws_set_params(h, W.warm_start_init(NP, 32, seed=seed))
+    rng = np.random.default_rng(seed)
+    losses = []
+    for step in range(steps):
+        idx = torch.tensor(rng.choice(n_train, B, replace=False), device="cuda")
+        losses.append(tomo.tomo_ws_train_step(h, s[idx].contiguous(), z[idx].contiguous(), B,
+                                              2e-3 if step < 0.7 * steps else 5e-4))
+    return float(np.mean(losses[:5])), float(np.mean(losses[-20:]))
 
 
 def run_reference(args):
@@ -314,6 +340,31 @@ def run_ours(args):
                "relres_max": float(pinfo["relres"].max()),
                "all_converged": bool((pinfo["status"] == 0).all() and (pinfo["relres"] <= TOL).all()),
                "preconditioner": "block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{-1} on the 150 x 150 torus"}
+        # the learned warm start (trained offline on other seeded frames) in front of the same PCG
+        learned = None
+        if not args.no_learned:
+            l0, l1 = train_warm_start(tomo, torch, h, cfg, layout, sub, seed=2000 + rank)
+            lopts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True,
+                                    warm_start=2)
+            for _ in range(args.warmup):
+                tomo.tomo_solve(h, s, F, lopts, z, phi)
+            levs, linfos = [], []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                linfos.append(tomo.tomo_solve(h, s, F, lopts, z, phi))
+                e1.record(stream)
+                levs.append((e0, e1))
+            torch.cuda.synchronize()
+            lms = sum(a.elapsed_time(b) for a, b in levs)
+            linfo = linfos[-1]
+            learned = {"value": world * F * args.steps / (lms / 1000.0), "unit": UNIT, "ms_per_step": lms / args.steps,
+                       "iters_mean": float(linfo["iters"].mean()),
+                       "all_converged": bool((linfo["status"] == 0).all() and (linfo["relres"] <= TOL).all()),
+                       "training": {"frames": 256, "steps": 200, "loss_first": l0, "loss_last": l1,
+                                    "network": "3x3 CNN 12-32-32-32-12, FP32, warm start of the PCG"}}
         total_ms = sum(step_ms)
         if dist:
             t = torch.tensor([total_ms], device="cuda")
@@ -378,7 +429,7 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "pcg": pcg,
+            "pcg": pcg, "learned_pcg": learned,
             "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                       "relres_max": float(info["relres"].max()), "all_converged": ok,
                       "refinements_max": int(info["refinements"].max()),

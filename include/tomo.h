@@ -114,7 +114,8 @@ typedef struct {
                               CG drives its recursive residual to 0.7 tol       */
     int max_iter;          /* CG iterations per call, over all refinement passes   */
     int max_refine;        /* FP64 true-residual restarts after the first pass    */
-    int warm_start;        /* 1: zeta_dev holds the initial guess on entry        */
+    int warm_start;        /* 1: zeta_dev holds the initial guess on entry;
+                              2: the initial guess is the warm-start network's  */
     int check_every;       /* iterations between host convergence checks (>= 1)   */
     int precond;           /* 1: preconditioned CG with the block-circulant M     */
 } tomo_solve_opts;
@@ -210,6 +211,42 @@ tomo_status tomo_solve_host(tomo_handle* h, const float* slopes_host, int batch,
 /* Number of kernel launches the handle has issued since creation (a counter
  * kept by the library, for launch accounting). */
 long long tomo_launch_count(const tomo_handle* h);
+
+/* Learned warm start (an addition to the paper, which starts its solvers from
+ * zero or from the previous estimate, Sec. 5).  A convolutional network maps
+ * the slope grids of one frame to an initial zeta for tomo_solve
+ * (opts->warm_start = 2):
+ *   input  [2 nGS][n][n]  slopes * in_scale on the subaperture grid, 0 off W_s;
+ *   layers 3x3 convolutions 2nGS -> hidden -> hidden -> hidden -> 2nGS, zero
+ *          padding, ReLU after the first three, FP32;
+ *   output zeta_0 = out_scale * (last layer at the valid subapertures).
+ * With precond_input (needs the preconditioner, cfg->precond) the input has
+ * 4 nGS planes, [slopes * in_scale, M^{-1} slopes / out_scale], and the output
+ * is zeta_0 = pre_gain M^{-1} slopes + out_scale * (last layer): the network learns a
+ * local correction of the block-circulant estimate (whose errors sit at the
+ * pupil edges and obstruction, where the circulant model misses the mask).
+ * Parameters are one FP32 vector: per layer W [Cout][Cin][3][3] then b [Cout].
+ * Training (tomo_ws_train_step, Adam) minimises ||zeta_0 - zeta*||^2 / ||zeta*||^2
+ * over (slopes, zeta*) pairs, zeta* from tomo_solve.  Device buffers are
+ * [batch][N] as elsewhere; batch <= max_batch for the gradient calls.
+ * tomo_ws_init: once per handle (EINVAL on a second call, hidden > 32 or
+ * 2 nGS > 32).  Parameters start at zero: set them with tomo_ws_set_params,
+ * which also resets the optimiser state.  tomo_ws_gradient returns the
+ * parameter gradient and the loss without updating (for checks). */
+tomo_status tomo_ws_init(tomo_handle* h, int hidden, int max_batch, float in_scale, float out_scale,
+                         int precond_input, float pre_gain);
+tomo_status tomo_ws_param_count(const tomo_handle* h, int* count);
+tomo_status tomo_ws_set_params(tomo_handle* h, const float* params_host, int count);
+tomo_status tomo_ws_get_params(const tomo_handle* h, float* params_host, int count);
+tomo_status tomo_ws_apply(tomo_handle* h, const float* slopes_dev, float* zeta_dev, int batch);
+tomo_status tomo_ws_gradient(tomo_handle* h, const float* slopes_dev, const float* zeta_target_dev, int batch,
+                             float* grad_host, double* loss_host);
+tomo_status tomo_ws_train_step(tomo_handle* h, const float* slopes_dev, const float* zeta_target_dev, int batch,
+                               float lr, double* loss_host);
+
+/* y = M^{-1} x: the block-circulant preconditioner (see tomo_create) applied to
+ * `batch` frames, FP32.  EINVAL if the handle was created without it. */
+tomo_status tomo_apply_precond(tomo_handle* h, const float* x_dev, float* y_dev, int batch);
 
 /* Kernel timing.  With timing enabled, tomo_solve launches its CG iterations
  * eagerly (no CUDA graph) with a CUDA event on the handle's stream before and

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/tomo.h"
+#include "cnn.cuh"
 #include "kernels.cuh"
 
 using namespace tomo;
@@ -30,6 +31,27 @@ struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int B = -1, iters = 0, mode = 0;
     long long nodes = 0;
+};
+
+// Warm-start network state (see tomo_ws_* in include/tomo.h).
+struct WarmStartNet {
+    bool ready = false;
+    int layers = 4, maxB = 0, np = 0, step = 0;
+    int ch[5] = {0, 0, 0, 0, 0};
+    size_t offW[4] = {0, 0, 0, 0}, offb[4] = {0, 0, 0, 0};
+    float in_scale = 1.f, out_scale = 1.f;
+    bool dirty = true;                 // weight layouts need rebuilding
+    float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    float *Wt[4] = {nullptr, nullptr, nullptr, nullptr}, *Wb[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* zero_bias = nullptr;
+    float* act[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    float *d0 = nullptr, *d1 = nullptr, *gz = nullptr, *z = nullptr;
+    float* wpart = nullptr;
+    double *sums = nullptr, *loss = nullptr;
+    bool hybrid = false;               // input channels [s, M^{-1} s], output M^{-1} s + correction
+    float pre_scale = 1.f;             // scale of the M^{-1} s input channels
+    float pre_gain = 1.f;              // zeta_0 = pre_gain M^{-1} s + out_scale * network
+    float* zpre = nullptr;             // M^{-1} s of the current batch
 };
 
 struct tomo_handle {
@@ -77,6 +99,7 @@ struct tomo_handle {
     GraphCache graph;
     std::vector<void*> allocs;
     // kernel timing (tomo_set_kernel_timing): eager CG iterations with events
+    WarmStartNet ws;
     bool timing = false;
     double kt_ms[TOMO_NKERNELS] = {0};
     long long kt_n[TOMO_NKERNELS] = {0};
@@ -584,6 +607,64 @@ void release(tomo_handle* h) {
     delete h;
 }
 
+// y = W_s F^{-1} M(f) F W_s^T x (the block-circulant preconditioner), FP32
+tomo_status apply_pre(tomo_handle* h, const Launch& L, const float* x, float* y, int B) {
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1, h->d_tw32)));
+    CK((cols_mul<float>(L, h->g_ss, B, nullptr, h->X1, h->Y1, h->d_M32, h->d_tw32, true)));
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, nullptr, h->Y1, x, h->d_zero_var, y, nullptr,
+                                      h->d_tw32)));
+    return TOMO_OK;
+}
+
+// --- warm-start network -------------------------------------------------------
+tomo_status ws_layouts(tomo_handle* h, const Launch& L) {
+    WarmStartNet& w = h->ws;
+    if (!w.dirty) return TOMO_OK;
+    for (int l = 0; l < w.layers; ++l)
+        CK(weight_layouts(L, w.ch[l], w.ch[l + 1], w.params + w.offW[l], w.Wt[l], w.Wb[l]));
+    w.dirty = false;
+    return TOMO_OK;
+}
+
+// act[4] = network(slopes), zeta = gather(act[4]) * out_scale
+tomo_status ws_forward(tomo_handle* h, const Launch& L, const float* s, int B, float* zeta) {
+    WarmStartNet& w = h->ws;
+    TRY(ws_layouts(h, L));
+    CK(cnn_scatter(L, B, h->NP, h->n, h->n_vs, h->mt.rowcol, s, w.in_scale, w.act[0], w.ch[0]));
+    if (w.hybrid) {
+        TRY(apply_pre(h, L, s, w.zpre, B));
+        // channels NP..2NP-1 of the input grid: M^{-1} s * in_scale / out_scale
+        CK(cnn_scatter_planes(L, B, h->NP, 2 * h->NP, h->NP, h->n, h->n_vs, h->mt.rowcol, w.zpre,
+                              w.pre_scale, w.act[0]));
+    }
+    for (int l = 0; l < w.layers; ++l)
+        CK(conv_fwd(L, B, w.ch[l], w.ch[l + 1], h->n, w.act[l], w.Wt[l], w.params + w.offb[l], w.act[l + 1],
+                    l + 1 < w.layers));
+    if (zeta) {
+        CK(cnn_gather(L, B, h->NP, h->n, h->n_vs, h->mt.rowcol, w.act[w.layers], w.out_scale, zeta));
+        if (w.hybrid) CK(axpy_f32(L, (size_t)B * h->N, w.pre_gain, w.zpre, zeta));
+    }
+    return TOMO_OK;
+}
+
+// parameter gradient of loss(zeta) for dloss/dzeta = gz (valid entries), after ws_forward
+tomo_status ws_backward(tomo_handle* h, const Launch& L, int B) {
+    WarmStartNet& w = h->ws;
+    const size_t plane = (size_t)h->n * h->n;
+    CK(cnn_scatter(L, B, h->NP, h->n, h->n_vs, h->mt.rowcol, w.gz, w.out_scale, w.d0, h->NP));
+    float* dy = w.d0;
+    float* dx = w.d1;
+    for (int l = w.layers - 1; l >= 0; --l) {
+        if (l + 1 < w.layers) CK(relu_bwd(L, (size_t)B * w.ch[l + 1] * plane, w.act[l + 1], dy));
+        CK(conv_wgrad(L, B, w.ch[l], w.ch[l + 1], h->n, w.act[l], dy, w.wpart, w.grad + w.offW[l]));
+        if (l > 0) {
+            CK(conv_fwd(L, B, w.ch[l + 1], w.ch[l], h->n, dy, w.Wb[l], w.zero_bias, dx, false));
+            std::swap(dx, dy);
+        }
+    }
+    return TOMO_OK;
+}
+
 tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_opts& o, float* zeta, float* phase,
                         tomo_frame_info* info) {
     // the solve runs on the private stream, ordered after the caller's stream
@@ -592,7 +673,15 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
     CK(cudaEventRecord(h->ev_in, h->work));
     CK(cudaStreamWaitEvent(h->work, h->ev_in, 0));
     // the handle's x buffer holds zeta during the solve
-    if (o.warm_start) {
+    if (o.warm_start == 2) {
+        if (!h->ws.ready) return TOMO_EINVAL;
+        for (int b0 = 0; b0 < B; b0 += h->ws.maxB) {
+            const int nb = std::min(h->ws.maxB, B - b0);
+            TRY(ws_forward(h, L, s + (size_t)b0 * h->N, nb, h->x + (size_t)b0 * h->N));
+        }
+        TRY(apply_ss32(h, L, h->x, h->Ap, B, nullptr, nullptr));
+        CK(cg_init(L, B, h->N, h->nparts, s, h->Ap, h->x, h->r, h->p, h->Ap, h->init_part));
+    } else if (o.warm_start) {
         CK(cudaMemcpyAsync(h->x, zeta, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
         TRY(apply_ss32(h, L, h->x, h->Ap, B, nullptr, nullptr));
         CK(cg_init(L, B, h->N, h->nparts, s, h->Ap, h->x, h->r, h->p, h->Ap, h->init_part));
@@ -850,6 +939,130 @@ tomo_status tomo_solve_host(tomo_handle* h, const float* slopes, int batch, cons
                                cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_ws_init(tomo_handle* h, int hidden, int max_batch, float in_scale, float out_scale,
+                         int precond_input, float pre_gain) {
+    if (!h || hidden < 1 || hidden > 32 || max_batch < 1 || !(in_scale > 0) || !(out_scale > 0)) return TOMO_EINVAL;
+    if ((precond_input ? 2 : 1) * h->NP > 32 || (precond_input && !h->d_M32)) return TOMO_EINVAL;
+    WarmStartNet& w = h->ws;
+    if (w.ready) return TOMO_EINVAL;   // once per handle
+    w.hybrid = precond_input != 0;
+    const int ch[5] = {(w.hybrid ? 2 : 1) * h->NP, hidden, hidden, hidden, h->NP};
+    size_t off = 0;
+    for (int l = 0; l < 4; ++l) {
+        w.ch[l] = ch[l];
+        w.offW[l] = off;
+        off += (size_t)ch[l + 1] * ch[l] * 9;
+        w.offb[l] = off;
+        off += ch[l + 1];
+    }
+    w.ch[4] = ch[4];
+    w.np = (int)off;
+    w.maxB = max_batch;
+    w.in_scale = in_scale;
+    w.out_scale = out_scale;
+    w.pre_scale = 1.f / out_scale;
+    w.pre_gain = pre_gain;
+    TRY(dalloc(h, &w.params, off));
+    TRY(dalloc(h, &w.grad, off));
+    TRY(dalloc(h, &w.m, off));
+    TRY(dalloc(h, &w.v, off));
+    for (int l = 0; l < 4; ++l) {
+        TRY(dalloc(h, &w.Wt[l], (size_t)ch[l + 1] * ch[l] * 9));
+        TRY(dalloc(h, &w.Wb[l], (size_t)ch[l + 1] * ch[l] * 9));
+    }
+    TRY(dalloc(h, &w.zero_bias, 32));
+    const size_t plane = (size_t)h->n * h->n;
+    const int cmax = std::max(hidden, ch[0]);
+    for (int l = 0; l < 5; ++l) TRY(dalloc(h, &w.act[l], (size_t)max_batch * ch[l] * plane));
+    TRY(dalloc(h, &w.d0, (size_t)max_batch * cmax * plane));
+    TRY(dalloc(h, &w.d1, (size_t)max_batch * cmax * plane));
+    TRY(dalloc(h, &w.gz, (size_t)max_batch * h->N));
+    TRY(dalloc(h, &w.z, (size_t)max_batch * h->N));
+    TRY(dalloc(h, &w.zpre, (size_t)max_batch * h->N));
+    TRY(dalloc(h, &w.wpart, conv_wgrad_parts(max_batch, cmax, cmax, h->n)));
+    TRY(dalloc(h, &w.sums, 512));
+    TRY(dalloc(h, &w.loss, 1));
+    CK(cudaMemsetAsync(w.params, 0, sizeof(float) * off, h->stream));
+    CK(cudaMemsetAsync(w.m, 0, sizeof(float) * off, h->stream));
+    CK(cudaMemsetAsync(w.v, 0, sizeof(float) * off, h->stream));
+    CK(cudaMemsetAsync(w.zero_bias, 0, sizeof(float) * 32, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    w.step = 0;
+    w.dirty = true;
+    w.ready = true;
+    return TOMO_OK;
+}
+
+tomo_status tomo_ws_param_count(const tomo_handle* h, int* count) {
+    if (!h || !count || !h->ws.ready) return TOMO_EINVAL;
+    *count = h->ws.np;
+    return TOMO_OK;
+}
+
+tomo_status tomo_ws_set_params(tomo_handle* h, const float* params, int count) {
+    if (!h || !params || !h->ws.ready || count != h->ws.np) return TOMO_EINVAL;
+    CK(cudaMemcpyAsync(h->ws.params, params, sizeof(float) * count, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->ws.m, 0, sizeof(float) * count, h->stream));
+    CK(cudaMemsetAsync(h->ws.v, 0, sizeof(float) * count, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->ws.step = 0;
+    h->ws.dirty = true;
+    return TOMO_OK;
+}
+
+tomo_status tomo_ws_get_params(const tomo_handle* h, float* params, int count) {
+    if (!h || !params || !h->ws.ready || count != h->ws.np) return TOMO_EINVAL;
+    CK(cudaMemcpyAsync(params, h->ws.params, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_ws_apply(tomo_handle* h, const float* slopes, float* zeta, int batch) {
+    if (!h || !slopes || !zeta || batch < 0 || !h->ws.ready) return TOMO_EINVAL;
+    Launch L = launch_of(h);
+    for (int b0 = 0; b0 < batch; b0 += h->ws.maxB) {
+        const int nb = std::min(h->ws.maxB, batch - b0);
+        TRY(ws_forward(h, L, slopes + (size_t)b0 * h->N, nb, zeta + (size_t)b0 * h->N));
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_ws_gradient(tomo_handle* h, const float* slopes, const float* target, int batch, float* grad_host,
+                             double* loss_host) {
+    if (!h || !slopes || !target || !h->ws.ready || batch < 1 || batch > h->ws.maxB) return TOMO_EINVAL;
+    Launch L = launch_of(h);
+    WarmStartNet& w = h->ws;
+    TRY(ws_forward(h, L, slopes, batch, w.z));
+    CK(loss_grad(L, (size_t)batch * h->N, w.z, target, w.sums, w.gz, w.loss));
+    TRY(ws_backward(h, L, batch));
+    if (grad_host) CK(cudaMemcpyAsync(grad_host, w.grad, sizeof(float) * w.np, cudaMemcpyDeviceToHost, h->stream));
+    if (loss_host) CK(cudaMemcpyAsync(loss_host, w.loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_ws_train_step(tomo_handle* h, const float* slopes, const float* target, int batch, float lr,
+                               double* loss_host) {
+    if (!(lr > 0)) return TOMO_EINVAL;
+    TRY(tomo_ws_gradient(h, slopes, target, batch, nullptr, loss_host));
+    Launch L = launch_of(h);
+    WarmStartNet& w = h->ws;
+    w.step += 1;
+    CK(adam(L, w.np, w.params, w.grad, w.m, w.v, lr, w.step));
+    w.dirty = true;
+    return TOMO_OK;
+}
+
+tomo_status tomo_apply_precond(tomo_handle* h, const float* x, float* y, int batch) {
+    if (!h || !x || !y || batch < 0 || x == y || !h->d_M32) return TOMO_EINVAL;
+    Launch L = launch_of(h);
+    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        TRY(apply_pre(h, L, x + (size_t)f0 * h->N, y + (size_t)f0 * h->N, B));
+    }
     return TOMO_OK;
 }
 

@@ -56,6 +56,8 @@ FRAME_INFO_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("s
 EXPORTS = ("tomo_create", "tomo_layout", "tomo_apply_css", "tomo_apply_css_noalloc", "tomo_apply_css_f64",
            "tomo_apply_cos",
            "tomo_solve", "tomo_solve_host", "tomo_launch_count", "tomo_set_kernel_timing",
+           "tomo_apply_precond", "tomo_ws_init", "tomo_ws_param_count", "tomo_ws_set_params", "tomo_ws_get_params", "tomo_ws_apply",
+           "tomo_ws_gradient", "tomo_ws_train_step",
            "tomo_get_kernel_timing", "tomo_destroy", "tomo_strerror")
 KERNEL_NAMES = ("rows_fwd", "cols_mul", "rows_inv", "cg_scalars")
 
@@ -89,6 +91,14 @@ def lib(path=None):
     L.tomo_solve_host.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_launch_count.argtypes = [vp]
     L.tomo_launch_count.restype = ctypes.c_longlong
+    L.tomo_ws_init.argtypes = [vp, i, i, ctypes.c_float, ctypes.c_float, i, ctypes.c_float]
+    L.tomo_apply_precond.argtypes = [vp, vp, vp, i]
+    L.tomo_ws_param_count.argtypes = [vp, ctypes.POINTER(i)]
+    L.tomo_ws_set_params.argtypes = [vp, vp, i]
+    L.tomo_ws_get_params.argtypes = [vp, vp, i]
+    L.tomo_ws_apply.argtypes = [vp, vp, vp, i]
+    L.tomo_ws_gradient.argtypes = [vp, vp, vp, i, vp, ctypes.POINTER(d)]
+    L.tomo_ws_train_step.argtypes = [vp, vp, vp, i, ctypes.c_float, ctypes.POINTER(d)]
     L.tomo_set_kernel_timing.argtypes = [vp, i]
     L.tomo_get_kernel_timing.argtypes = [vp, vp, vp, vp]
     L.tomo_destroy.argtypes = [vp]
@@ -181,7 +191,8 @@ def tomo_apply_cos(h, zeta, phase, batch):
     _check("tomo_apply_cos", lib().tomo_apply_cos(h, _dptr(zeta, torch.float32), _dptr(phase, torch.float32), batch))
 
 
-def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=False, check_every=32, precond=False):
+def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=0, check_every=32, precond=False):
+    """warm_start: 0 cold, 1 zeta holds the guess, 2 the warm-start network's guess."""
     return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every, int(bool(precond)))
 
 
@@ -206,6 +217,57 @@ def tomo_solve_host(h, slopes, batch, opts, zeta, phase=None):
 
 def tomo_launch_count(h):
     return lib().tomo_launch_count(h)
+
+
+def tomo_ws_init(h, hidden=32, max_batch=64, in_scale=1.0, out_scale=1.0, precond_input=False, pre_gain=1.0):
+    _check("tomo_ws_init", lib().tomo_ws_init(h, hidden, max_batch, in_scale, out_scale, int(bool(precond_input)),
+                                              pre_gain))
+
+
+def tomo_apply_precond(h, x, y, batch):
+    import torch
+    _check("tomo_apply_precond", lib().tomo_apply_precond(h, _dptr(x, torch.float32), _dptr(y, torch.float32), batch))
+
+
+def tomo_ws_param_count(h):
+    c = ctypes.c_int(0)
+    _check("tomo_ws_param_count", lib().tomo_ws_param_count(h, ctypes.byref(c)))
+    return c.value
+
+
+def tomo_ws_set_params(h, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check("tomo_ws_set_params", lib().tomo_ws_set_params(h, _hptr(p, np.float32), p.size))
+
+
+def tomo_ws_get_params(h):
+    p = np.zeros(tomo_ws_param_count(h), np.float32)
+    _check("tomo_ws_get_params", lib().tomo_ws_get_params(h, _hptr(p, np.float32), p.size))
+    return p
+
+
+def tomo_ws_apply(h, slopes, zeta, batch):
+    import torch
+    _check("tomo_ws_apply", lib().tomo_ws_apply(h, _dptr(slopes, torch.float32), _dptr(zeta, torch.float32), batch))
+
+
+def tomo_ws_gradient(h, slopes, target, batch):
+    """Returns (flat parameter gradient, loss) of the supervised loss, without updating."""
+    import torch
+    g = np.zeros(tomo_ws_param_count(h), np.float32)
+    loss = ctypes.c_double(0.0)
+    _check("tomo_ws_gradient", lib().tomo_ws_gradient(h, _dptr(slopes, torch.float32), _dptr(target, torch.float32),
+                                                      batch, _hptr(g, np.float32), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def tomo_ws_train_step(h, slopes, target, batch, lr):
+    import torch
+    loss = ctypes.c_double(0.0)
+    _check("tomo_ws_train_step", lib().tomo_ws_train_step(h, _dptr(slopes, torch.float32),
+                                                          _dptr(target, torch.float32), batch, lr,
+                                                          ctypes.byref(loss)))
+    return loss.value
 
 
 def tomo_set_kernel_timing(h, enable):

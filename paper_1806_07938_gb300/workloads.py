@@ -135,12 +135,13 @@ def _clean_frame(cfg, seed, f, screen_px, grids):
 N_CALIBRATION_FRAMES = 4
 
 
-def slope_frames(cfg, n_frames, seed=0, screen_px=512):
-    """Noisy slopes [frame][gs][x|y][n][n] (float64) and the per-GS noise sigma.
+def slope_frames(cfg, n_frames, seed=0, screen_px=512, first=0):
+    """Noisy slopes [frame][gs][x|y][n][n] (float64) of frames first .. first+n_frames-1
+    and the per-GS noise sigma.
 
     Returns (slopes, noise_sigma): noise_sigma[g] = noise_frac * rms of the
     noiseless slopes of guide star g over frames 0..3 of ``seed`` (always the
-    same frames, whatever ``n_frames`` is).
+    same frames, whatever ``n_frames`` and ``first`` are).
     """
     n, D = cfg["n"], cfg["D"]
     d = D / n
@@ -151,12 +152,46 @@ def slope_frames(cfg, n_frames, seed=0, screen_px=512):
     hy, hx = np.meshgrid(e, m, indexing="ij")     # (n+1, n) midpoints of horizontal edges
     grids = ((cx, cy), (vx, vy), (hx, hy))
     n_gs = len(cfg["gs"])
-    clean = [_clean_frame(cfg, seed, f, screen_px, grids)
-             for f in range(max(n_frames, N_CALIBRATION_FRAMES))]
-    calib = np.stack(clean[:N_CALIBRATION_FRAMES])
+    calib = np.stack([_clean_frame(cfg, seed, f, screen_px, grids) for f in range(N_CALIBRATION_FRAMES)])
     sigma = cfg["noise_frac"] * np.sqrt(np.mean(calib ** 2, axis=(0, 2, 3, 4)))
-    noisy = np.stack(clean[:n_frames])
-    for f in range(n_frames):
+    noisy = np.zeros((n_frames, n_gs, 2, n, n))
+    for i in range(n_frames):
+        f = first + i
+        noisy[i] = calib[f] if f < N_CALIBRATION_FRAMES else _clean_frame(cfg, seed, f, screen_px, grids)
         rng = _rng(seed, f, 999)
-        noisy[f] += sigma[:, None, None, None] * rng.standard_normal((n_gs, 2, n, n))
+        noisy[i] += sigma[:, None, None, None] * rng.standard_normal((n_gs, 2, n, n))
     return noisy, sigma
+
+
+def _frames_job(args):
+    cfg, n_frames, seed, first = args
+    return slope_frames(cfg, n_frames, seed=seed, first=first)
+
+
+def slope_frames_parallel(cfg, n_frames, seed=0, workers=None, chunk=8):
+    """slope_frames on a pool of `spawn` worker processes (identical result)."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    workers = workers or min(32, os.cpu_count() or 1)
+    jobs = [(cfg, min(chunk, n_frames - a), seed, a) for a in range(0, n_frames, chunk)]
+    if workers <= 1 or len(jobs) <= 1:
+        return slope_frames(cfg, n_frames, seed=seed)
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_frames_job, jobs))
+    return np.concatenate([p[0] for p in parts]), parts[0][1]
+
+
+def warm_start_init(n_planes, hidden, seed, last_gain=0.1):
+    """Seeded He-normal initial parameters of the warm-start network (flat FP32,
+    per layer W [Cout][Cin][3][3] then b [Cout]); the last layer scaled by last_gain."""
+    rng = np.random.default_rng(seed)
+    ch = [n_planes, hidden, hidden, hidden, n_planes]
+    out = []
+    for l in range(4):
+        co, ci = ch[l + 1], ch[l]
+        W = rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (9 * ci))
+        if l == 3:
+            W *= last_gain
+        out += [W.ravel(), 0.01 * rng.standard_normal(co)]
+    return np.concatenate(out).astype(np.float32)

@@ -203,6 +203,20 @@ def test_pcg_golden(T, name):
         assert info["iters"].mean() < infoc["iters"].mean()
 
 
+@pytest.mark.parametrize("n,eps,lgs", [(7, 0.2, True), (12, 0.28, False)])
+def test_apply_precond_matches_oracle(T, n, eps, lgs):
+    from oracle import precond
+    cfg = small_cfg(n=n, lgs=lgs, obstruction=eps, D=0.6 * n, noise=0.2)
+    with Handle(T, cfg, max_batch=2, precond=True) as H:
+        x = np.random.default_rng(n).standard_normal((2, H.info.N))
+        xd = dev(x)
+        yd = torch.empty_like(xd)
+        T.tomo_apply_precond(H.h, xd, yd, 2)
+        torch.cuda.synchronize()
+        ref = precond.apply(cfg, x, H.info.P)
+        assert relL2(yd.double().cpu().numpy(), ref) <= 1e-5
+
+
 def test_solve_zero_slopes(T):
     cfg = small_cfg(n=6, lgs=True)
     with Handle(T, cfg, max_batch=2) as H:

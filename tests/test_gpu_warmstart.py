@@ -1,0 +1,114 @@
+"""GPU checks of the learned warm start (tomo_ws_*) against the FP64 oracle
+network, and of what the trained network gains in the solve."""
+import numpy as np
+import pytest
+
+from conftest import small_cfg
+from oracle import cnn
+from oracle import geometry as geo
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_07938_gb300 import tomo
+    tomo.lib()
+    return tomo
+
+
+def init_params(NP, hidden, seed, last_gain=0.1, cin=None):
+    rng = np.random.default_rng(seed)
+    out = []
+    shapes = cnn.layer_shapes(NP, hidden)
+    if cin is not None:
+        shapes[0] = (hidden, cin)
+    for l, (co, ci) in enumerate(shapes):
+        W = rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (9 * ci))
+        if l == 3:
+            W *= last_gain
+        out += [W.ravel(), 0.01 * rng.standard_normal(co)]
+    return np.concatenate(out).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,hidden,B,hybrid", [(7, 5, 3, False), (7, 5, 3, True), (74, 32, 2, False)])
+def test_forward_and_gradient_match_oracle(T, n, hidden, B, hybrid):
+    from oracle import precond
+    cfg = small_cfg(n=n, n_gs=2 if n < 20 else 6, lgs=True, obstruction=0.2 if n < 20 else 0.28, D=0.527 * n)
+    h = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=B, precond=hybrid)
+    try:
+        info, _, _ = T.tomo_layout(h)
+        NP = 2 * len(cfg["gs"])
+        T.tomo_ws_init(h, hidden=hidden, max_batch=B, in_scale=0.5, out_scale=2.0, precond_input=hybrid, pre_gain=0.7)
+        params = init_params(NP, hidden, seed=n, last_gain=1.0, cin=2 * NP if hybrid else None)
+        T.tomo_ws_set_params(h, params)
+        assert np.array_equal(T.tomo_ws_get_params(h), params)
+        rng = np.random.default_rng(1)
+        s = rng.standard_normal((B, info.N)).astype(np.float32)
+        t = rng.standard_normal((B, info.N)).astype(np.float32)
+        sd = torch.tensor(s, device="cuda")
+        td = torch.tensor(t, device="cuda")
+        z = torch.empty_like(sd)
+        T.tomo_ws_apply(h, sd, z, B)
+        torch.cuda.synchronize()
+        pre = precond.apply(cfg, s, info.P) if hybrid else None
+        z_ref, _ = cnn.forward(params.astype(np.float64), s, n, cfg["obstruction"], hidden, 0.5, 2.0, pre, 0.7)
+        zg = z.double().cpu().numpy()
+        assert np.linalg.norm(zg - z_ref) / np.linalg.norm(z_ref) <= 1e-5
+        g, loss = T.tomo_ws_gradient(h, sd, td, B)
+        loss_ref, g_ref = cnn.loss_and_grad(params.astype(np.float64), s, t, n, cfg["obstruction"], hidden, 0.5, 2.0,
+                                            pre, 0.7)
+        assert abs(loss - loss_ref) <= 1e-5 * loss_ref
+        assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) <= 1e-4
+    finally:
+        T.tomo_destroy(h)
+
+
+def test_training_gains_iterations(T):
+    from paper_1806_07938_gb300 import workloads as W
+    cfg = W.config("lgs_mid")
+    n_train, n_test = 256, 32
+    full, sigma = W.slope_frames(cfg, n_train + n_test, seed=7)
+    cfg["noise_sigma"] = [float(x) for x in sigma]
+    mask = geo.subaperture_mask(cfg["n"], cfg["obstruction"])
+    s = full[..., mask].reshape(n_train + n_test, -1).astype(np.float32)
+    B = 32
+    h = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=B, precond=True)
+    try:
+        sd = torch.tensor(s, device="cuda")
+        zs = torch.zeros_like(sd)
+        for b0 in range(0, n_train + n_test, B):
+            T.tomo_solve(h, sd[b0:b0 + B].contiguous(), B, T.solve_opts(tol=1e-5, precond=True), zs[b0:b0 + B])
+        z_np = zs.cpu().numpy()
+        NP = 2 * len(cfg["gs"])
+        T.tomo_ws_init(h, hidden=32, max_batch=B, in_scale=float(1.0 / s.std()), out_scale=float(z_np.std()))
+        T.tomo_ws_set_params(h, init_params(NP, 32, seed=11))
+        rng = np.random.default_rng(5)
+        losses = []
+        for step in range(600):
+            idx = rng.choice(n_train, B, replace=False)
+            xb = sd[idx].contiguous()
+            tb = zs[idx].contiguous()
+            losses.append(T.tomo_ws_train_step(h, xb, tb, B, 2e-3 if step < 400 else 5e-4))
+        print('loss first/last', np.mean(losses[:10]), np.mean(losses[-50:]))
+        assert np.mean(losses[-50:]) < 0.85 * np.mean(losses[:10])
+        # held-out frames: warm start from the network vs cold start
+        st = sd[n_train:].contiguous()
+        z0 = torch.empty_like(st)
+        T.tomo_ws_apply(h, st, z0, n_test)
+        zt = zs[n_train:].cpu().numpy()
+        rel = np.linalg.norm(z0.cpu().numpy() - zt) / np.linalg.norm(zt)
+        zc = torch.zeros_like(st)
+        cold = T.tomo_solve(h, st, n_test, T.solve_opts(tol=1e-4, precond=True), zc)
+        zw = torch.zeros_like(st)
+        warm = T.tomo_solve(h, st, n_test, T.solve_opts(tol=1e-4, precond=True, warm_start=2), zw)
+        print(f"warm start: held-out relative error {rel:.3f}; PCG iterations cold {cold['iters'].mean():.1f} "
+              f"warm {warm['iters'].mean():.1f}; final loss {np.mean(losses[-50:]):.3f}")
+        assert (warm["status"] == 0).all() and (warm["relres"] <= 1e-4).all()
+        assert rel < 1.0
+        assert warm["iters"].mean() < cold["iters"].mean()
+    finally:
+        T.tomo_destroy(h)
