@@ -97,6 +97,8 @@ typedef struct {
     int max_batch;         /* frames per call the workspaces are sized for        */
     int precond;           /* 1: also build the block-circulant preconditioner    */
     double precond_floor;  /* c of the preconditioner (see tomo_solve_opts), 0 = 3 */
+    int mode_removal;      /* 1: remove tip, tilt and focus (Sec. 2.F, mode
+                              removal; see tomo_solve)                           */
 } tomo_config;
 
 typedef struct {
@@ -201,6 +203,36 @@ tomo_status tomo_apply_cos(tomo_handle* h, const float* zeta_dev, float* phase_d
 tomo_status tomo_solve(tomo_handle* h, const float* slopes_dev, int batch,
                        const tomo_solve_opts* opts, float* zeta_dev, float* phase_dev,
                        tomo_frame_info* info_host);
+
+/* tomo_solve with a Fried parameter per frame (Sec. 2.A: the von Karman
+ * covariance of every layer is proportional to r0^{-5/3}, with the Cn^2
+ * fractions fixed).  Frame f solves
+ *     (c_f W_s Sigma_ss W_s^T + nu_f Sigma_eta_eta) zeta_f = s_f,
+ *     phi_f = c_f W_phi Sigma_phi_s W_s^T zeta_f,
+ * with c_f = (r0_host[f] / cfg.r0)^{-5/3} and nu_f = noise_scale_host[f]
+ * (all 1 when noise_scale_host is NULL: the noise variance of the
+ * configuration), so one batch can mix frames taken under different seeing.
+ * r0_host [batch] metres at 500 nm, > 0; noise_scale_host [batch] >= 0 or
+ * NULL; both host memory, read before the call returns.  The preconditioner,
+ * if used, is the configuration's one scaled by 1 / c_f (exact when
+ * nu_f = c_f).  Other arguments and results as tomo_solve; TOMO_EINVAL for a
+ * non-positive or non-finite r0 or a negative noise scale. */
+tomo_status tomo_solve_r0(tomo_handle* h, const float* slopes_dev, int batch,
+                          const double* r0_host, const double* noise_scale_host,
+                          const tomo_solve_opts* opts, float* zeta_dev, float* phase_dev,
+                          tomo_frame_info* info_host);
+
+/* With cfg.mode_removal = 1 (split tomography, Sec. 2.F "Mode removal"),
+ * tomo_solve, tomo_solve_r0 and tomo_solve_host solve instead
+ *     M_s W_s (Sigma_ss + Sigma_eta_eta) W_s^T M_s zeta = M_s s,
+ *     phi = M_phi W_phi Sigma_phi_s W_s^T M_s zeta,
+ * with M_s = I - Z_s Z_s^+ per WFS (Z_s: the 2 n_vs x 3 slopes of tip x,
+ * tilt y and focus x^2 + y^2 on the valid subapertures) and M_phi the same on
+ * the valid phase points (Z_phi: x, y, x^2 + y^2).  The returned zeta is
+ * M_s zeta (the minimum-norm solution when the solve converges), relres is
+ * ||M_s s - M_s A M_s zeta|| / ||M_s s||, and tomo_apply_css / tomo_apply_cos
+ * keep applying the operators without the projections.  The paper applies
+ * it to laser guide stars; here it applies to every WFS of the handle. */
 
 /* tomo_solve on host buffers: copies slopes in and zeta / phase out around the
  * solve (phase_host may be NULL).  Returns after the stream has finished. */

@@ -112,6 +112,15 @@ def system_matrix(cfg):
     return A
 
 
+def system_matrix_r0(cfg, r0, noise_scale=1.0):
+    """A of a frame seen with Fried parameter r0 (same Cn^2 fractions): Sigma_ss
+    formed at that r0 from the point covariances, plus noise_scale times the
+    configuration's noise variance (Eq. SAap1 for that frame)."""
+    A = css_dense(dict(cfg, r0=float(r0)))
+    A[np.diag_indices_from(A)] += float(noise_scale) * noise_variance(cfg)
+    return A
+
+
 def cos_exact(cfg, target):
     """Sigma_phi_beta_s on valid phase points x valid slopes (FP64), Eq. covIterative2.
 

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "../../include/tomo.h"
@@ -82,6 +83,17 @@ struct tomo_handle {
     float2* d_Kc32 = nullptr;
     float2* d_M32 = nullptr;           // block-circulant preconditioner spectra (nullptr: not built)
     double* d_zero_var = nullptr;      // zero diagonal for the preconditioner pass
+    // per-frame scales of the solve (tomo_solve_r0): (c_f, nu_f) of
+    // A_f = c_f Sigma_ss + nu_f Sigma_eta_eta, and (1 / c_f, 0) for the preconditioner
+    double2* d_fscale = nullptr;
+    double2* d_fscale_pre = nullptr;
+    bool fscale_unit = false;          // both hold the unit scales
+    // tip/tilt/focus removal: orthonormal mode bases of one WFS's slopes
+    // [3][2 n_vs] and of the phase points [3][n_vphi]
+    bool modes = false;
+    double* d_Qs = nullptr;
+    double* d_Qp = nullptr;
+    float* s_proj = nullptr;           // M_s s of the current chunk
     int* d_iidx = nullptr;
     float* d_iw = nullptr;
     // workspaces
@@ -140,6 +152,25 @@ tomo_status dalloc(tomo_handle* h, Tp** ptr, size_t count) {
         if (s_ != TOMO_OK) return s_;      \
     } while (0)
 
+// Orthonormal rows spanning the three columns of Z ([3][len], row-major),
+// modified Gram-Schmidt applied twice (FP64); false if Z is rank deficient.
+bool orthonormal_rows(std::vector<double>& Z, int len) {
+    for (int k = 0; k < 3; ++k) {
+        double* zk = Z.data() + (size_t)k * len;
+        const double n0 = std::sqrt(std::inner_product(zk, zk + len, zk, 0.0));
+        for (int pass = 0; pass < 2; ++pass)
+            for (int j = 0; j < k; ++j) {
+                const double* zj = Z.data() + (size_t)j * len;
+                const double c = std::inner_product(zk, zk + len, zj, 0.0);
+                for (int e = 0; e < len; ++e) zk[e] -= c * zj[e];
+            }
+        const double nk = std::sqrt(std::inner_product(zk, zk + len, zk, 0.0));
+        if (!(nk > 1e-9 * n0)) return false;
+        for (int e = 0; e < len; ++e) zk[e] /= nk;
+    }
+    return true;
+}
+
 // Radix plan for P (factors 2, 3, 4, 5, 7); false if P has another prime factor.
 bool make_plan(int P, FftPlan* pl) {
     pl->P = P;
@@ -185,12 +216,13 @@ Launch launch_of(tomo_handle* h) { return Launch{h->stream, &h->launches}; }
 
 // Sigma_ss + noise on FP32 vectors; with cg != nullptr, one CG product (see rows_fwd).
 tomo_status apply_ss32(tomo_handle* h, const Launch& L, const float* x, float* y, int B, const FrameState* st,
-                       const CgVecs* cg) {
+                       const CgVecs* cg, const double2* fscale = nullptr) {
     CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, x, cg, st, h->X1, h->d_tw32)));
     CK((cols_mul<float>(L, h->g_ss, B, st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
     const float* xin = cg ? cg->p : x;
     float* yout = cg ? cg->Ap : y;
-    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, st, h->Y1, xin, h->d_noise_var, yout, cg, h->d_tw32)));
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, st, h->Y1, xin, h->d_noise_var, fscale, yout, cg,
+                                      h->d_tw32)));
     return TOMO_OK;
 }
 
@@ -198,21 +230,24 @@ CgVecs cg_vecs(tomo_handle* h, int mode, double* dots) {
     return CgVecs{h->x, h->r, h->p, h->Ap, h->rr_part, dots, mode, h->z, h->w};
 }
 
-tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double* y, int B) {
+tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double* y, int B,
+                       const double2* fscale = nullptr) {
     CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1d, h->d_tw64)));
     CK((cols_mul<double>(L, h->g_ss, B, nullptr, h->X1d, h->Y1d, h->d_K64, h->d_tw64, false)));
-    CK((rows_inv_masked<double, double>(L, h->g_ss, h->mt, B, nullptr, h->Y1d, x, h->d_noise_var, y, nullptr,
-                                        h->d_tw64)));
+    CK((rows_inv_masked<double, double>(L, h->g_ss, h->mt, B, nullptr, h->Y1d, x, h->d_noise_var, fscale, y,
+                                        nullptr, h->d_tw64)));
     return TOMO_OK;
 }
 
-tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi, int B) {
+tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi, int B,
+                     const double2* fscale = nullptr) {
     CK((rows_fwd<float, float>(L, h->g_os, h->mt, B, z, nullptr, nullptr, h->Xc, h->d_twc32)));
     const size_t kc_stride = (size_t)h->g_os.nh * h->Pc * h->cos_layers * h->NP;
     for (int t = 0; t < h->n_targets; ++t) {
         CK((cols_mul<float>(L, h->g_os, B, nullptr, h->Xc, h->Yc, h->d_Kc32 + t * kc_stride, h->d_twc32, false)));
         CK((rows_inv_dense<float>(L, h->g_os, B, h->Yc, h->Ydc, h->d_twc32)));
-        CK(interp(L, B, h->n_targets, t, h->cos_layers, h->m, h->n_vphi, h->Ydc, h->d_iidx, h->d_iw, phi));
+        CK(interp(L, B, h->n_targets, t, h->cos_layers, h->m, h->n_vphi, h->Ydc, h->d_iidx, h->d_iw, fscale,
+                  phi));
     }
     return TOMO_OK;
 }
@@ -247,8 +282,9 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, bool pcg, std::vec
         TRY(mark(0));
         CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
         TRY(mark(1));
-        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->Ap, &cg,
-                                          h->d_tw32)));
+        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->d_fscale,
+                                          h->Ap, &cg, h->d_tw32)));
+        if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, h->d_Qs, h->st, h->Ap, h->p, &cg));
         TRY(mark(2));
         CK(cg_scalars(L, B, h->NP, h->rr_part, h->dot_part, h->st));
         TRY(mark(3));
@@ -260,15 +296,17 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, bool pcg, std::vec
     TRY(mark(0));
     CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_M32, h->d_tw32, true)));
     TRY(mark(1));
-    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->r, h->d_zero_var, h->z, &cgM,
-                                      h->d_tw32)));
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->r, h->d_zero_var, h->d_fscale_pre,
+                                      h->z, &cgM, h->d_tw32)));
+    if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, h->d_Qs, h->st, h->z, h->r, &cgM));
     TRY(mark(2));
     CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, h->z, nullptr, h->st, h->X1, h->d_tw32)));
     TRY(mark(0));
     CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
     TRY(mark(1));
-    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->z, h->d_noise_var, h->w, &cgA,
-                                      h->d_tw32)));
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->z, h->d_noise_var, h->d_fscale,
+                                      h->w, &cgA, h->d_tw32)));
+    if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, h->d_Qs, h->st, h->w, h->z, &cgA));
     TRY(mark(2));
     CK(pcg_scalars(L, B, h->NP, h->rr_part, h->dot_part_M, h->dot_part, h->st));
     TRY(mark(3));
@@ -326,6 +364,7 @@ tomo_status validate(const tomo_config* c) {
     if (!(c->D > 0) || !(c->obstruction >= 0) || !(c->obstruction < 1) || !(c->r0 > 0) || !(c->L0 > 0))
         return TOMO_EINVAL;
     if (!(c->precond_floor >= 0)) return TOMO_EINVAL;
+    if (c->mode_removal != 0 && c->mode_removal != 1) return TOMO_EINVAL;
     if (c->max_batch < 1 || c->max_batch > 4096) return TOMO_EINVAL;
     const double H = c->gs[0].height;
     for (int g = 0; g < c->n_gs; ++g) {
@@ -389,6 +428,38 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         for (int j = 0; j <= n; ++j)
             if (h->phase_mask[(size_t)i * (n + 1) + j]) { pv_i.push_back(i); pv_j.push_back(j); }
     h->n_vphi = (int)pv_i.size();
+    if (c->mode_removal) {
+        // Z_s: slopes of tip x, tilt y and focus x^2 + y^2 on one WFS; the
+        // two-point slopes (Appendix A.2) of these modes at the subaperture
+        // centre (xc, yc) are (d, 0), (0, d) and (2 d xc, 2 d yc); the common
+        // factor d does not change the span
+        const int len = 2 * h->n_vs;
+        std::vector<double> Zs((size_t)3 * len, 0.0);
+        int e = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                if (h->subap_mask[(size_t)i * n + j]) {
+                    const double xc = (j + 0.5 - 0.5 * n) * h->d, yc = (i + 0.5 - 0.5 * n) * h->d;
+                    Zs[e] = 1.0;
+                    Zs[(size_t)len + h->n_vs + e] = 1.0;
+                    Zs[(size_t)2 * len + e] = 2.0 * xc;
+                    Zs[(size_t)2 * len + h->n_vs + e] = 2.0 * yc;
+                    ++e;
+                }
+        std::vector<double> Zp((size_t)3 * h->n_vphi);
+        for (int v = 0; v < h->n_vphi; ++v) {
+            const double x = (pv_j[v] - 0.5 * n) * h->d, y = (pv_i[v] - 0.5 * n) * h->d;
+            Zp[v] = x;
+            Zp[(size_t)h->n_vphi + v] = y;
+            Zp[(size_t)2 * h->n_vphi + v] = x * x + y * y;
+        }
+        if (!orthonormal_rows(Zs, len) || !orthonormal_rows(Zp, h->n_vphi)) return TOMO_EINVAL;
+        h->modes = true;
+        TRY(dalloc(h, &h->d_Qs, Zs.size()));
+        TRY(dalloc(h, &h->d_Qp, Zp.size()));
+        TRY(upload(h, Zs.data(), h->d_Qs, sizeof(double) * Zs.size()));
+        TRY(upload(h, Zp.data(), h->d_Qp, sizeof(double) * Zp.size()));
+    }
 
     // --- layers: B_k(0) = c_v (L0/r0)^{5/3} f_k and cone factors ------------------
     const double cv = std::pow(24.0 / 5.0 * std::tgamma(6.0 / 5.0), 5.0 / 6.0) * std::tgamma(11.0 / 6.0) *
@@ -590,6 +661,9 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     TRY(dalloc(h, &h->s_stage, B * h->N));
     TRY(dalloc(h, &h->z_stage, B * h->N));
     TRY(dalloc(h, &h->phi_stage, B * h->n_targets * h->n_vphi));
+    TRY(dalloc(h, &h->d_fscale, B));
+    if (h->modes) TRY(dalloc(h, &h->s_proj, B * h->N));
+    TRY(dalloc(h, &h->d_fscale_pre, B));
     CK(cudaMallocHost(&h->h_nactive, sizeof(int)));
     CK(cudaStreamSynchronize(h->stream));
     return TOMO_OK;
@@ -611,8 +685,8 @@ void release(tomo_handle* h) {
 tomo_status apply_pre(tomo_handle* h, const Launch& L, const float* x, float* y, int B) {
     CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1, h->d_tw32)));
     CK((cols_mul<float>(L, h->g_ss, B, nullptr, h->X1, h->Y1, h->d_M32, h->d_tw32, true)));
-    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, nullptr, h->Y1, x, h->d_zero_var, y, nullptr,
-                                      h->d_tw32)));
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, nullptr, h->Y1, x, h->d_zero_var, nullptr, y,
+                                      nullptr, h->d_tw32)));
     return TOMO_OK;
 }
 
@@ -665,13 +739,60 @@ tomo_status ws_backward(tomo_handle* h, const Launch& L, int B) {
     return TOMO_OK;
 }
 
+// Per-frame operator scales of the next B frames on the work stream:
+// A_f = c_f Sigma_ss + nu_f Sigma_eta_eta (c, nu host arrays; null = all 1),
+// and the preconditioner scale 1 / c_f.
+tomo_status set_fscale(tomo_handle* h, int B, const double* c, const double* nu) {
+    if (!c && !nu) {
+        if (h->fscale_unit) return TOMO_OK;
+        B = h->max_batch;
+    }
+    std::vector<double2> fs(B), fp(B);
+    for (int f = 0; f < B; ++f) {
+        const double cf = c ? c[f] : 1.0, nf = nu ? nu[f] : 1.0;
+        fs[f] = make_double2(cf, nf);
+        fp[f] = make_double2(1.0 / cf, 0.0);
+    }
+    CK(cudaMemcpyAsync(h->d_fscale, fs.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, h->work));
+    CK(cudaMemcpyAsync(h->d_fscale_pre, fp.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, h->work));
+    CK(cudaStreamSynchronize(h->work));
+    h->fscale_unit = !c && !nu;
+    return TOMO_OK;
+}
+
 tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_opts& o, float* zeta, float* phase,
-                        tomo_frame_info* info) {
+                        tomo_frame_info* info, const double* c_scale = nullptr, const double* nu_scale = nullptr) {
     // the solve runs on the private stream, ordered after the caller's stream
     // and before anything the caller enqueues next
     Launch L{h->work, &h->launches};
-    CK(cudaEventRecord(h->ev_in, h->work));
+    TRY(set_fscale(h, B, c_scale, nu_scale));
+    CK(cudaEventRecord(h->ev_in, h->stream));
     CK(cudaStreamWaitEvent(h->work, h->ev_in, 0));
+    const int ms_len = 2 * h->n_vs;
+    if (h->modes) {
+        // right-hand side M_s s
+        CK(cudaMemcpyAsync(h->s_proj, s, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
+        CK(mode_project<float>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->s_proj, nullptr, nullptr));
+        s = h->s_proj;
+    }
+    // A x0 for a warm start x0 (projected first under mode removal)
+    auto start_from_x = [&]() -> tomo_status {
+        if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->x, nullptr, nullptr));
+        TRY(apply_ss32(h, L, h->x, h->Ap, B, nullptr, nullptr, h->d_fscale));
+        if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->Ap, nullptr, nullptr));
+        CK(cg_init(L, B, h->N, h->nparts, s, h->Ap, h->x, h->r, h->p, h->Ap, h->init_part));
+        return TOMO_OK;
+    };
+    // FP64 true residual r = s - A x (M_s s - M_s A M_s x under mode removal)
+    auto true_res = [&](int max_refine) -> tomo_status {
+        CK(to_f64(L, (size_t)B * h->N, h->x, h->xd));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->xd, nullptr, nullptr));
+        TRY(apply_ss64(h, L, h->xd, h->yd, B, h->d_fscale));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->yd, nullptr, nullptr));
+        CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->res_part));
+        CK(true_residual_finalize(L, B, h->nparts, h->res_part, o.tol, max_refine, h->st));
+        return TOMO_OK;
+    };
     // the handle's x buffer holds zeta during the solve
     if (o.warm_start == 2) {
         if (!h->ws.ready) return TOMO_EINVAL;
@@ -679,12 +800,10 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             const int nb = std::min(h->ws.maxB, B - b0);
             TRY(ws_forward(h, L, s + (size_t)b0 * h->N, nb, h->x + (size_t)b0 * h->N));
         }
-        TRY(apply_ss32(h, L, h->x, h->Ap, B, nullptr, nullptr));
-        CK(cg_init(L, B, h->N, h->nparts, s, h->Ap, h->x, h->r, h->p, h->Ap, h->init_part));
+        TRY(start_from_x());
     } else if (o.warm_start) {
         CK(cudaMemcpyAsync(h->x, zeta, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
-        TRY(apply_ss32(h, L, h->x, h->Ap, B, nullptr, nullptr));
-        CK(cg_init(L, B, h->N, h->nparts, s, h->Ap, h->x, h->r, h->p, h->Ap, h->init_part));
+        TRY(start_from_x());
     } else {
         CK(cg_init(L, B, h->N, h->nparts, s, nullptr, h->x, h->r, h->p, h->Ap, h->init_part));
     }
@@ -705,10 +824,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         if (h->timing) collect_timing(h, marks);
         if (*h->h_nactive == 0) {
             // FP64 true residual s - A zeta and restart of the frames above tol
-            CK(to_f64(L, (size_t)B * h->N, h->x, h->xd));
-            TRY(apply_ss64(h, L, h->xd, h->yd, B));
-            CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->res_part));
-            CK(true_residual_finalize(L, B, h->nparts, h->res_part, o.tol, o.max_refine, h->st));
+            TRY(true_res(o.max_refine));
             CK(count_active(L, B, h->st, h->d_nactive));
             CK(cudaMemcpyAsync(h->h_nactive, h->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, h->work));
             CK(cudaStreamSynchronize(h->work));
@@ -723,10 +839,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
                 if (f.active) { f.active = 0; f.status = TOMO_FRAME_MAXIT; }
             CK(cudaMemcpyAsync(h->st, tmp.data(), sizeof(FrameState) * B, cudaMemcpyHostToDevice, h->work));
             CK(cudaStreamSynchronize(h->work));
-            CK(to_f64(L, (size_t)B * h->N, h->x, h->xd));
-            TRY(apply_ss64(h, L, h->xd, h->yd, B));
-            CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->res_part));
-            CK(true_residual_finalize(L, B, h->nparts, h->res_part, o.tol, 0, h->st));
+            TRY(true_res(0));
             break;
         }
         if (h->timing) {
@@ -737,8 +850,13 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         }
         total_iters += chunk;
     }
+    if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->x, nullptr, nullptr));
     CK(cudaMemcpyAsync(zeta, h->x, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
-    if (phase) TRY(apply_os(h, L, h->x, phase, B));
+    if (phase) {
+        TRY(apply_os(h, L, h->x, phase, B, h->d_fscale));
+        if (h->modes)
+            CK(mode_project<float>(L, B, h->n_vphi, h->n_targets, h->d_Qp, nullptr, phase, nullptr, nullptr));
+    }
     CK(cudaEventRecord(h->ev_out, h->work));
     CK(cudaStreamWaitEvent(h->stream, h->ev_out, 0));
     if (info) {
@@ -834,8 +952,8 @@ tomo_status tomo_apply_css_noalloc(tomo_handle* h, const float* x, float* y, int
         float* yb = y + (size_t)f0 * h->N;
         CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, xb, nullptr, nullptr, X1, h->d_tw32)));
         CK((cols_mul<float>(L, h->g_ss, B, nullptr, X1, Y1, h->d_K32, h->d_tw32, true)));
-        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, nullptr, Y1, xb, h->d_noise_var, yb, nullptr,
-                                          h->d_tw32)));
+        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, nullptr, Y1, xb, h->d_noise_var, nullptr, yb,
+                                          nullptr, h->d_tw32)));
     }
     return TOMO_OK;
 }
@@ -915,6 +1033,27 @@ tomo_status tomo_solve(tomo_handle* h, const float* slopes, int batch, const tom
         const int B = std::min(h->max_batch, batch - f0);
         TRY(solve_chunk(h, slopes + (size_t)f0 * h->N, B, o, zeta + (size_t)f0 * h->N,
                         phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr, info ? info + f0 : nullptr));
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_solve_r0(tomo_handle* h, const float* slopes, int batch, const double* r0, const double* noise_scale,
+                          const tomo_solve_opts* opts, float* zeta, float* phase, tomo_frame_info* info) {
+    if (!h || !slopes || !zeta || !r0 || batch < 0) return TOMO_EINVAL;
+    tomo_solve_opts o = opts ? *opts : default_opts();
+    if (!(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 || o.check_every < 1) return TOMO_EINVAL;
+    // von Karman covariances scale as r0^{-5/3} (B(0) = c_v (L0 / r0)^{5/3})
+    std::vector<double> c(batch);
+    for (int f = 0; f < batch; ++f) {
+        if (!(r0[f] > 0) || !std::isfinite(r0[f])) return TOMO_EINVAL;
+        if (noise_scale && !(noise_scale[f] >= 0 && std::isfinite(noise_scale[f]))) return TOMO_EINVAL;
+        c[f] = std::pow(r0[f] / h->r0, -5.0 / 3.0);
+    }
+    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        TRY(solve_chunk(h, slopes + (size_t)f0 * h->N, B, o, zeta + (size_t)f0 * h->N,
+                        phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr, info ? info + f0 : nullptr,
+                        c.data() + f0, noise_scale ? noise_scale + f0 : nullptr));
     }
     return TOMO_OK;
 }

@@ -535,7 +535,8 @@ __device__ __forceinline__ void load_row_pairs(const C* __restrict__ src, int m,
 template <typename T, typename TIn, int PC>
 __global__ void __launch_bounds__(kThreads, TOMO_MIN_BLOCKS)
 k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T>* __restrict__ Y1T,
-                  const TIn* __restrict__ xin, const double* __restrict__ noise_var, TIn* __restrict__ y,
+                  const TIn* __restrict__ xin, const double* __restrict__ noise_var,
+                  const double2* __restrict__ fscale, TIn* __restrict__ y,
                   CgVecs cg, const cplx_t<T>* __restrict__ twg) {
     using C = cplx_t<T>;
     constexpr int G = kFftGroup;
@@ -560,7 +561,9 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
     __syncthreads();
     // gather the valid outputs (W_s), add the noise term, CG dot products
     const size_t vbase = ((size_t)f * g.NPout + pp) * mt.n_vs;
-    const TIn nv = (TIn)noise_var[pp];
+    const double2 fs = fscale ? fscale[f] : make_double2(1.0, 1.0);
+    const TIn cs = (TIn)fs.x;
+    const TIn nv = (TIn)(noise_var[pp] * fs.y);
     const bool cgm = cg.p != nullptr;
     const float* __restrict__ vr = cg.r;
     const int* __restrict__ rowcol = mt.rowcol;
@@ -572,7 +575,7 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
         const TIn xi = __ldg(xin + vbase + e);
         const float ri = cgm ? __ldg(vr + vbase + e) : 0.f;
         const T v = reinterpret_cast<const T*>(F + (row >> 1) * RS + col)[row & 1];
-        const TIn out = (TIn)v + nv * xi;
+        const TIn out = cs * (TIn)v + nv * xi;
         y[vbase + e] = out;
         if (cgm) {
             acc += (double)xi * (double)out;
@@ -593,14 +596,14 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
 
 template <typename T, typename TIn>
 cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const FrameState* st,
-                            const cplx_t<T>* Y1T, const TIn* xin, const double* noise_var, TIn* y, const CgVecs* cg,
-                            const cplx_t<T>* tw) {
+                            const cplx_t<T>* Y1T, const TIn* xin, const double* noise_var, const double2* fscale,
+                            TIn* y, const CgVecs* cg, const cplx_t<T>* tw) {
     const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     const size_t smem = rows_smem<T>(g, g.m);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
 #define TOMO_L(PC)                                                                                   \
     k_rows_inv_masked<T, TIn, PC><<<dim3(g.NPout, B), kThreads, smem, L.stream>>>(g, mt, st, Y1T, xin, \
-                                                                                  noise_var, y, cgv, tw)
+                                                                                  noise_var, fscale, y, cgv, tw)
     TOMO_DISPATCH_P(g.plan.P, TOMO_L)
 #undef TOMO_L
     count(L);
@@ -1228,7 +1231,8 @@ cudaError_t pack_hermitian(const Launch& L, int P, int NP, const float2* Kfull, 
 
 // phi[f][t][v] = sum_k sum_c w[k][v][c] Yd[f][k][idx[k][v][c]]  (Eq. interp, sum over layers)
 __global__ void k_interp(int B, int T_all, int t, int n_layers, int m, int n_vphi, const float* __restrict__ Yd,
-                         const int* __restrict__ idx, const float* __restrict__ w, float* __restrict__ phi) {
+                         const int* __restrict__ idx, const float* __restrict__ w, const double2* __restrict__ fscale,
+                         float* __restrict__ phi) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     const int f = blockIdx.y;
     if (v >= n_vphi) return;
@@ -1239,12 +1243,14 @@ __global__ void k_interp(int B, int T_all, int t, int n_layers, int m, int n_vph
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc += w[o + c] * Y[idx[o + c]];
     }
+    if (fscale) acc *= (float)fscale[f].x;
     phi[((size_t)f * T_all + t) * n_vphi + v] = acc;
 }
 
 cudaError_t interp(const Launch& L, int B, int T_all, int t, int n_layers, int m, int n_vphi, const float* Yd,
-                   const int* idx, const float* w, float* phi) {
-    k_interp<<<dim3((n_vphi + 127) / 128, B), 128, 0, L.stream>>>(B, T_all, t, n_layers, m, n_vphi, Yd, idx, w, phi);
+                   const int* idx, const float* w, const double2* fscale, float* phi) {
+    k_interp<<<dim3((n_vphi + 127) / 128, B), 128, 0, L.stream>>>(B, T_all, t, n_layers, m, n_vphi, Yd, idx, w,
+                                                                     fscale, phi);
     count(L);
     return cudaGetLastError();
 }
@@ -1296,10 +1302,10 @@ template cudaError_t cols_mul<double>(const Launch&, const MvmGeom&, int, const 
                                       const double2*, const double2*, bool);
 template cudaError_t rows_inv_masked<float, float>(const Launch&, const MvmGeom&, const MaskTables&, int,
                                                    const FrameState*, const float2*, const float*, const double*,
-                                                   float*, const CgVecs*, const float2*);
+                                                   const double2*, float*, const CgVecs*, const float2*);
 template cudaError_t rows_inv_masked<double, double>(const Launch&, const MvmGeom&, const MaskTables&, int,
                                                      const FrameState*, const double2*, const double*, const double*,
-                                                     double*, const CgVecs*, const double2*);
+                                                     const double2*, double*, const CgVecs*, const double2*);
 template cudaError_t rows_inv_dense<float>(const Launch&, const MvmGeom&, int, const float2*, float*, const float2*);
 
 }  // namespace tomo

@@ -95,13 +95,15 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
 // Full [nh][NP][P][NP] spectrum -> Hermitian upper-triangle layout [nh][P][e].
 cudaError_t pack_hermitian(const Launch& L, int P, int NP, const float2* Kfull, float2* Kpacked);
 
-// Row-inverse pass to masked output (Sigma_ss): y = crop/mask(IFFT rows) +
-// noise_var[plane] * xin.  CG mode (cg != nullptr; xin = cg->p, y = cg->Ap):
-// also the partial sums p^T Ap, r^T Ap, Ap^T Ap per (frame, plane).
+// Row-inverse pass to masked output (Sigma_ss): y = c_f crop/mask(IFFT rows) +
+// nu_f noise_var[plane] * xin, with (c_f, nu_f) = fscale[frame] ((1, 1) when
+// fscale is null).  CG mode (cg != nullptr; xin = cg->p, y = cg->Ap): also the
+// partial sums p^T Ap, r^T Ap, Ap^T Ap per (frame, plane).
 template <typename T, typename TIn>
 cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B,
                             const FrameState* st, const cplx_t<T>* Y1T, const TIn* xin,
-                            const double* noise_var, TIn* y, const CgVecs* cg, const cplx_t<T>* tw);
+                            const double* noise_var, const double2* fscale, TIn* y, const CgVecs* cg,
+                            const cplx_t<T>* tw);
 
 // Row-inverse pass to a dense m x m output per plane: Yd [B][NPout][m][m].
 template <typename T>
@@ -130,6 +132,17 @@ cudaError_t true_residual(const Launch& L, int B, int N, int nparts, const float
 cudaError_t true_residual_finalize(const Launch& L, int B, int nparts, const double* parts,
                                    double tol, int max_refine, FrameState* st);
 cudaError_t count_active(const Launch& L, int B, const FrameState* st, int* n_active);
+
+// --- mode removal (modes.cu) -------------------------------------------------
+// y [B][nblk][len] <- y - Q^T (Q y) per (frame, block), Q [3][len] orthonormal
+// rows (FP64).  Slopes: nblk = n_gs blocks of len = 2 n_vs; phase: nblk =
+// n_targets blocks of len = n_vphi.  With cg != nullptr (slopes, FP32): also
+// the partial sums xin^T y, r^T y, y^T y of the projected y per plane into
+// cg->dot_part, replacing those of the row-inverse pass that produced y.
+// Frames with st[f].active == 0 are skipped when st is not null.
+template <typename TV>
+cudaError_t mode_project(const Launch& L, int B, int len, int nblk, const double* Q, const FrameState* st, TV* y,
+                         const float* xin, const CgVecs* cg);
 
 // --- setup ------------------------------------------------------------------
 struct VkParams {
@@ -164,8 +177,9 @@ cudaError_t gen_cos(const Launch& L, int n, int m, int P, int NP, double d, int 
 // K [nh][NPin][P][NPout] (plane index p*NPin + q), FP64 and FP32 copies.
 cudaError_t spectra(const Launch& L, int P, int npl, int NPin, const FftPlan& plan,
                     const double* G, double2* H, const double2* tw64, double2* K64, float2* K32);
-// Bilinear interpolation of the projection: phi [B][T][n_vphi] (target t slot).
+// Bilinear interpolation of the projection: phi [B][T][n_vphi] (target t slot),
+// times fscale[frame].x when fscale is not null.
 cudaError_t interp(const Launch& L, int B, int T_all, int t, int n_layers, int m, int n_vphi,
-                   const float* Yd, const int* idx, const float* w, float* phi);
+                   const float* Yd, const int* idx, const float* w, const double2* fscale, float* phi);
 
 }  // namespace tomo

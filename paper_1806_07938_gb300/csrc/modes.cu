@@ -1,0 +1,103 @@
+// Tip/tilt/focus removal (Sec. 2.F, mode removal for laser guide stars).
+//
+// M_s,i = I - Z_s,i Z_s,i^+ removes from the 2 n_vs slopes of WFS i the
+// slopes of tip, tilt and focus; with an orthonormal basis Q of the columns
+// of Z_s,i (3 x 2 n_vs, the same for every WFS since all share one
+// subaperture grid), M_s,i y = y - Q^T (Q y).  M_phi does the same on the
+// valid phase points with the basis of x, y and x^2 + y^2.  Both are
+// O(n_vs) per WFS: two passes over the block, three dot products.
+#include "kernels.cuh"
+
+namespace tomo {
+
+namespace {
+
+inline void count(const Launch& L) {
+    if (L.counter) ++*L.counter;
+}
+
+constexpr int kModeThreads = 256;
+
+// Block-wide sums of V doubles; the result is valid in every thread.
+template <int V>
+__device__ __forceinline__ void block_sums(double (&v)[V], double (*red)[kModeThreads / 32]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        double a = v[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[k][warp] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        double s = 0.0;
+        for (int w = 0; w < kModeThreads / 32; ++w) s += red[k][w];
+        v[k] = s;
+    }
+    __syncthreads();
+}
+
+// One block per (block index, frame): y[blk] -= Q^T (Q y[blk]) over len
+// entries.  With dots != nullptr (FP32 CG vectors) also the partial sums
+// xin^T y, r^T y, y^T y of the projected y for the two halves of the block
+// (the x- and y-slope planes), stored like the row-inverse pass stores them.
+template <typename TV>
+__global__ void __launch_bounds__(kModeThreads)
+k_mode_project(int len, int nblk, const double* __restrict__ Q, const FrameState* st, TV* __restrict__ y,
+               const float* __restrict__ xin, const float* __restrict__ r, double* __restrict__ dots) {
+    __shared__ double red[6][kModeThreads / 32];
+    const int blk = blockIdx.x, f = blockIdx.y;
+    if (st && !st[f].active) return;
+    TV* yb = y + ((size_t)f * nblk + blk) * len;
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const double v = (double)yb[e];
+        c[0] += Q[e] * v;
+        c[1] += Q[len + e] * v;
+        c[2] += Q[2 * len + e] * v;
+    }
+    block_sums<3>(c, red);
+    const int half = len / 2;
+    double d[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const size_t base = ((size_t)f * nblk + blk) * len;
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const double v = (double)yb[e] - (c[0] * Q[e] + c[1] * Q[len + e] + c[2] * Q[2 * len + e]);
+        const TV out = (TV)v;
+        yb[e] = out;
+        if (dots) {
+            const int h = e < half ? 0 : 3;
+            const double o = (double)out;
+            d[h + 0] += (double)xin[base + e] * o;
+            d[h + 1] += (double)r[base + e] * o;
+            d[h + 2] += o * o;
+        }
+    }
+    if (dots) {
+        block_sums<6>(d, red);
+        if (threadIdx.x < 6) {
+            const int plane = 2 * blk + threadIdx.x / 3;
+            dots[((size_t)f * 2 * nblk + plane) * 3 + threadIdx.x % 3] = d[threadIdx.x];
+        }
+    }
+}
+
+}  // namespace
+
+template <typename TV>
+cudaError_t mode_project(const Launch& L, int B, int len, int nblk, const double* Q, const FrameState* st, TV* y,
+                         const float* xin, const CgVecs* cg) {
+    if (B <= 0) return cudaSuccess;
+    if (cg && (!xin || (len & 1))) return cudaErrorInvalidValue;
+    k_mode_project<TV><<<dim3(nblk, B), kModeThreads, 0, L.stream>>>(
+        len, nblk, Q, st, y, cg ? xin : nullptr, cg ? cg->r : nullptr, cg ? cg->dot_part : nullptr);
+    count(L);
+    return cudaGetLastError();
+}
+
+template cudaError_t mode_project<float>(const Launch&, int, int, int, const double*, const FrameState*, float*,
+                                         const float*, const CgVecs*);
+template cudaError_t mode_project<double>(const Launch&, int, int, int, const double*, const FrameState*, double*,
+                                          const float*, const CgVecs*);
+
+}  // namespace tomo

@@ -32,7 +32,7 @@ class tomo_config(ctypes.Structure):
                 ("n_targets", ctypes.c_int), ("target_x", ctypes.POINTER(ctypes.c_double)),
                 ("target_y", ctypes.POINTER(ctypes.c_double)),
                 ("fft_P", ctypes.c_int), ("fft_Pcos", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("precond", ctypes.c_int), ("precond_floor", ctypes.c_double)]
+                ("precond", ctypes.c_int), ("precond_floor", ctypes.c_double), ("mode_removal", ctypes.c_int)]
 
 
 class tomo_layout_info(ctypes.Structure):
@@ -55,7 +55,7 @@ FRAME_INFO_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("s
 
 EXPORTS = ("tomo_create", "tomo_layout", "tomo_apply_css", "tomo_apply_css_noalloc", "tomo_apply_css_f64",
            "tomo_apply_cos",
-           "tomo_solve", "tomo_solve_host", "tomo_launch_count", "tomo_set_kernel_timing",
+           "tomo_solve", "tomo_solve_r0", "tomo_solve_host", "tomo_launch_count", "tomo_set_kernel_timing",
            "tomo_apply_precond", "tomo_ws_init", "tomo_ws_param_count", "tomo_ws_set_params", "tomo_ws_get_params", "tomo_ws_apply",
            "tomo_ws_gradient", "tomo_ws_train_step",
            "tomo_get_kernel_timing", "tomo_destroy", "tomo_strerror")
@@ -89,6 +89,7 @@ def lib(path=None):
     L.tomo_apply_cos.argtypes = [vp, vp, vp, i]
     L.tomo_solve.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_solve_host.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
+    L.tomo_solve_r0.argtypes = [vp, vp, i, vp, vp, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_launch_count.argtypes = [vp]
     L.tomo_launch_count.restype = ctypes.c_longlong
     L.tomo_ws_init.argtypes = [vp, i, i, ctypes.c_float, ctypes.c_float, i, ctypes.c_float]
@@ -131,7 +132,7 @@ def _hptr(a, dtype):
     return ctypes.c_void_p(a.ctypes.data)
 
 
-def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_floor=0.0):
+def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_floor=0.0, mode_removal=False):
     """tomo_config from the plain-number system description; keeps its arrays alive."""
     n_gs = len(cfg["gs"])
     gs = (tomo_gs * n_gs)()
@@ -144,15 +145,17 @@ def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_fl
     tx = (ctypes.c_double * nt)(*[t[0] for t in cfg["targets"]])
     ty = (ctypes.c_double * nt)(*[t[1] for t in cfg["targets"]])
     c = tomo_config(cfg["D"], cfg["obstruction"], cfg["n"], n_gs, gs, nl, lh, lf, cfg["r0"], cfg["L0"],
-                    nt, tx, ty, fft_P, fft_Pcos, max_batch, int(bool(precond)), float(precond_floor))
+                    nt, tx, ty, fft_P, fft_Pcos, max_batch, int(bool(precond)), float(precond_floor),
+                    int(bool(mode_removal)))
     c._keep = (gs, lh, lf, tx, ty)
     return c
 
 
-def tomo_create(cfg, stream=None, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_floor=0.0):
+def tomo_create(cfg, stream=None, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_floor=0.0,
+                mode_removal=False):
     """Creates a handle; ``stream`` is a torch.cuda.Stream or None (legacy default)."""
     L = lib()
-    c = make_config(cfg, max_batch, fft_P, fft_Pcos, precond, precond_floor)
+    c = make_config(cfg, max_batch, fft_P, fft_Pcos, precond, precond_floor, mode_removal)
     h = ctypes.c_void_p()
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
     _check("tomo_create", L.tomo_create(ctypes.byref(c), s, ctypes.byref(h)))
@@ -202,6 +205,22 @@ def tomo_solve(h, slopes, batch, opts, zeta, phase=None):
     info = np.zeros(batch, FRAME_INFO_DTYPE)
     _check("tomo_solve", lib().tomo_solve(
         h, _dptr(slopes, torch.float32), batch, ctypes.byref(opts), _dptr(zeta, torch.float32),
+        _dptr(phase, torch.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)))
+    return info
+
+
+def tomo_solve_r0(h, slopes, batch, r0, opts, zeta, phase=None, noise_scale=None):
+    """Device solve with a Fried parameter per frame (r0, noise_scale: host
+    float64 arrays [batch]); returns the per-frame info."""
+    import torch
+    r0 = np.ascontiguousarray(r0, dtype=np.float64)
+    ns = None if noise_scale is None else np.ascontiguousarray(noise_scale, dtype=np.float64)
+    if r0.shape != (batch,) or (ns is not None and ns.shape != (batch,)):
+        raise ValueError("r0 and noise_scale need one value per frame")
+    info = np.zeros(batch, FRAME_INFO_DTYPE)
+    _check("tomo_solve_r0", lib().tomo_solve_r0(
+        h, _dptr(slopes, torch.float32), batch, _hptr(r0, np.float64),
+        _hptr(ns, np.float64) if ns is not None else None, ctypes.byref(opts), _dptr(zeta, torch.float32),
         _dptr(phase, torch.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)))
     return info
 

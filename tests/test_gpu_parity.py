@@ -217,6 +217,90 @@ def test_apply_precond_matches_oracle(T, n, eps, lgs):
         assert relL2(yd.double().cpu().numpy(), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("pcg,noise", [(False, "fixed"), (True, "fixed"), (False, "scaled")])
+def test_solve_r0_matches_oracle(T, pcg, noise):
+    # four seeings in one batch, chunked (max_batch 3): frame f solves
+    # (Sigma_ss(r0_f) + nu_f Sigma_eta_eta) zeta = s_f, Sigma_ss(r0_f) formed
+    # by the oracle at that r0 from the point covariances
+    cfg = small_cfg(n=7, lgs=True, obstruction=0.2, D=4.2, noise=0.15,
+                    targets=((0.0, 0.0), (10e-6, -5e-6)))
+    r0 = np.array([0.10, 0.133, 0.167, 0.20])
+    c = (r0 / cfg["r0"]) ** (-5.0 / 3.0)
+    nu = None if noise == "fixed" else np.array([0.5, 1.0, 2.0, 4.0])
+    with Handle(T, cfg, max_batch=3, precond=pcg) as H:
+        s = np.random.default_rng(5).standard_normal((4, H.info.N))
+        sd = dev(s)
+        zd = torch.zeros_like(sd)
+        phi = torch.empty((4, 2, H.info.n_vphi), dtype=torch.float32, device="cuda")
+        # tol 3e-5: a few times the floor that storing zeta in FP32 sets on
+        # these small, well-conditioned systems
+        info = T.tomo_solve_r0(H.h, sd, 4, r0, T.solve_opts(tol=3e-5, max_iter=20000, max_refine=5, precond=pcg),
+                               zd, phi, noise_scale=nu)
+        torch.cuda.synchronize()
+        z, phi = zd.double().cpu().numpy(), phi.double().cpu().numpy()
+        print("r0", info)
+        assert (info["status"] == 0).all() and (info["relres"] <= 3e-5).all()
+        sig2 = min(cfg["noise_sigma"]) ** 2
+        for f in range(4):
+            nuf = 1.0 if nu is None else nu[f]
+            A = cov.system_matrix_r0(cfg, r0[f], nuf)
+            zs = solve.solve_cholesky(A, s[f])
+            assert np.linalg.norm(z[f] - zs) <= info["relres"][f] * np.linalg.norm(s[f]) / (nuf * sig2)
+            assert relL2(z[f], zs) <= 1e-3
+            for t in range(2):
+                ref = cov.cos_interp(dict(cfg, r0=r0[f]), t) @ zs
+                assert relL2(phi[f, t], ref) <= 2e-3
+        # the frames differ: a single-r0 solve of the same slopes gives another zeta
+        z1, _, info1 = H.solve(s, tol=3e-5, max_iter=20000, max_refine=5, precond=pcg)
+        assert relL2(z1[0], z[0]) > 0.05
+        # and a plain solve after the per-frame one is back on the configuration's operator
+        zs0 = solve.solve_cholesky(cov.system_matrix(cfg), s[0])
+        assert np.linalg.norm(z1[0] - zs0) <= info1["relres"][0] * np.linalg.norm(s[0]) / sig2
+    with Handle(T, cfg, max_batch=2) as H:
+        sd = dev(np.ones((1, H.info.N)))
+        zd = torch.zeros_like(sd)
+        for bad in ([0.0], [-0.1], [np.inf]):
+            with pytest.raises(T.TomoError):
+                T.tomo_solve_r0(H.h, sd, 1, np.array(bad), T.solve_opts(), zd)
+        with pytest.raises(T.TomoError):
+            T.tomo_solve_r0(H.h, sd, 1, np.array([0.1]), T.solve_opts(), zd, noise_scale=np.array([-1.0]))
+
+
+@pytest.mark.parametrize("lgs,pcg", [(False, False), (True, False), (True, True)])
+def test_mode_removal_matches_oracle(T, lgs, pcg):
+    # split tomography: tip/tilt/focus removed from every WFS and from the
+    # estimate; zeta is the minimum-norm solution of M_s A M_s zeta = M_s s
+    from oracle import modes
+    cfg = small_cfg(n=8, lgs=lgs, obstruction=0.2, D=4.8, noise=0.15, targets=((0.0, 0.0), (12e-6, 0.0)))
+    A = cov.system_matrix(cfg)
+    rng = np.random.default_rng(21)
+    s = rng.standard_normal((3, A.shape[0]))
+    zs, phis = modes.reconstruct(cfg, s.T, A)
+    with Handle(T, cfg, max_batch=2, precond=pcg, mode_removal=True) as H:
+        z, phi, info = H.solve(s, tol=3e-5, max_iter=20000, max_refine=5, precond=pcg)
+        print("modes", info)
+        assert (info["status"] == 0).all() and (info["relres"] <= 3e-5).all()
+        Ms = modes.slope_removal(cfg)
+        assert (modes.relative_residual(cfg, A, s.T, z.T) <= 3.5e-5).all()
+        # on range(M_s), M_s A M_s >= sigma^2 I, so the error of zeta (which the
+        # library returns projected) is at most the residual over sigma^2
+        bound = info["relres"] * np.linalg.norm(s @ Ms, axis=1) / min(cfg["noise_sigma"]) ** 2
+        assert (np.linalg.norm(z - zs.T, axis=1) <= bound).all()
+        assert np.abs(z @ Ms - z).max() <= 1e-5 * np.abs(z).max()
+        for t in range(2):
+            assert relL2(phi[:, t], phis[t].T) <= 2e-3
+        # blind to the removed modes in the measurements
+        Zs = modes.slope_modes(cfg)
+        add = np.concatenate([Zs @ rng.standard_normal((3, 3)) for _ in cfg["gs"]]).T
+        z2, phi2, info2 = H.solve(s + 5 * add, tol=3e-5, max_iter=20000, max_refine=5, precond=pcg)
+        assert (info2["status"] == 0).all()
+        assert relL2(phi2, phi) <= 2e-3
+        # without removal the estimate differs
+    with Handle(T, cfg, max_batch=2) as H:
+        _, phi_full, _ = H.solve(s, tol=3e-5, max_iter=20000, max_refine=5)
+        assert relL2(phi_full, phi) > 0.05
+
+
 def test_solve_zero_slopes(T):
     cfg = small_cfg(n=6, lgs=True)
     with Handle(T, cfg, max_batch=2) as H:

@@ -170,3 +170,26 @@ def test_new_grid_covariance_is_toeplitz():
 def test_new_grid_size_rule():
     cfg = small_cfg(n=74, lgs=True, layers=((0.0, 0.5), (20000.0, 0.5)))
     assert cov.new_grid_size(cfg) == 97      # ceil(74 / (1 - 20/90)) + 1
+
+
+@pytest.mark.parametrize("lgs", [False, True])
+def test_covariance_scales_as_r0_to_minus_five_thirds(lgs):
+    # von Karman: B(rho) = c_v (L0/r0)^{5/3} * (a function of rho / L0), so every
+    # covariance (slope-slope and phase-slope) scales as r0^{-5/3} at fixed Cn^2
+    # fractions; the per-frame r0 system of the solver relies on it
+    cfg = small_cfg(n=5, lgs=lgs, obstruction=0.2, D=3.0)
+    base = cov.css_dense(cfg)
+    for r0 in (0.10, 0.2):
+        c = (r0 / cfg["r0"]) ** (-5.0 / 3.0)
+        got = cov.css_dense(dict(cfg, r0=r0))
+        assert np.abs(got - c * base).max() <= 1e-12 * np.abs(c * base).max()
+        F = c * cov.cos_interp(cfg, 0)
+        assert np.abs(cov.cos_interp(dict(cfg, r0=r0), 0) - F).max() <= 1e-12 * np.abs(F).max()
+        # and not as r0^{+5/3} or r0^{-5/6}
+        assert np.abs(got - base).max() > 0.3 * np.abs(base).max()
+    A = cov.system_matrix_r0(cfg, cfg["r0"])
+    assert np.array_equal(A, cov.system_matrix(cfg))
+    # the noise term is the configuration's, times the frame's noise scale
+    A2 = cov.system_matrix_r0(cfg, 0.1, noise_scale=2.5)
+    nv = cov.noise_variance(cfg)
+    assert np.allclose(np.diag(A2) - np.diag(cov.css_dense(dict(cfg, r0=0.1))), 2.5 * nv, rtol=1e-13)
