@@ -120,7 +120,17 @@ typedef struct {
                               2: the initial guess is the warm-start network's  */
     int check_every;       /* iterations between host convergence checks (>= 1)   */
     int precond;           /* 1: preconditioned CG with the block-circulant M     */
+    int method;            /* TOMO_METHOD_CG (0) or TOMO_METHOD_MINRES (1)         */
 } tomo_solve_opts;
+
+/* Krylov method of tomo_solve (tomo_solve_opts.method).  The paper tests CG
+ * and MINRES, both unpreconditioned (Sec. 2.G).  MINRES runs in its
+ * conjugate-residual form: for the symmetric positive (semi)definite systems
+ * here each iterate minimises ||s - A zeta|| over the Krylov space, with one
+ * operator product per iteration; it cannot be combined with precond = 1
+ * (TOMO_EINVAL).  tomo_frame_info.iters counts operator products of the
+ * iteration loop in both methods. */
+enum { TOMO_METHOD_CG = 0, TOMO_METHOD_MINRES = 1 };
 
 typedef struct {
     int iters;             /* CG iterations summed over refinement passes         */

@@ -261,7 +261,13 @@ tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi
 // r^T z), w = A z (three passes, z^T w), and the per-frame scalars.
 //
 // With marks != nullptr every kernel is bracketed by events (kernel timing).
-tomo_status iteration(tomo_handle* h, const Launch& L, int B, bool pcg, std::vector<std::pair<int, int>>* marks) {
+//
+// One MINRES iteration (conjugate-residual form): the previous update and FFT
+// of r (row-forward), w = A r with r^T w, Ap^T w, w^T w (column and
+// row-inverse passes), and the per-frame scalars.
+enum IterKind { kIterCG = 0, kIterPCG = 1, kIterMINRES = 2 };
+
+tomo_status iteration(tomo_handle* h, const Launch& L, int B, int kind, std::vector<std::pair<int, int>>* marks) {
     int last = -1;
     auto mark = [&](int slot) -> tomo_status {
         if (!marks) return TOMO_OK;
@@ -276,7 +282,21 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, bool pcg, std::vec
     };
     // slot encoding: pair (start event * 8 + kernel class, end event)
     TRY(mark(0));
-    if (!pcg) {
+    if (kind == kIterMINRES) {
+        const CgVecs cg = cg_vecs(h, 3, h->dot_part);
+        CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32)));
+        TRY(mark(0));
+        CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
+        TRY(mark(1));
+        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->r, h->d_noise_var, h->d_fscale,
+                                          h->w, &cg, h->d_tw32)));
+        if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, h->d_Qs, h->st, h->w, h->r, &cg));
+        TRY(mark(2));
+        CK(mr_scalars(L, B, h->NP, h->rr_part, h->dot_part, h->st));
+        TRY(mark(3));
+        return TOMO_OK;
+    }
+    if (kind == kIterCG) {
         const CgVecs cg = cg_vecs(h, 1, h->dot_part);
         CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32)));
         TRY(mark(0));
@@ -327,8 +347,8 @@ void collect_timing(tomo_handle* h, std::vector<std::pair<int, int>>& marks) {
     h->ev.clear();
 }
 
-tomo_status build_graph(tomo_handle* h, int B, int iters, bool pcg) {
-    if (h->graph.exec && h->graph.B == B && h->graph.iters == iters && h->graph.mode == (int)pcg) return TOMO_OK;
+tomo_status build_graph(tomo_handle* h, int B, int iters, int kind) {
+    if (h->graph.exec && h->graph.B == B && h->graph.iters == iters && h->graph.mode == kind) return TOMO_OK;
     if (h->graph.exec) {
         cudaGraphExecDestroy(h->graph.exec);
         h->graph.exec = nullptr;
@@ -337,7 +357,7 @@ tomo_status build_graph(tomo_handle* h, int B, int iters, bool pcg) {
     CK(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
     Launch Lc{h->work, &h->launches};
     tomo_status s = TOMO_OK;
-    for (int i = 0; i < iters && s == TOMO_OK; ++i) s = iteration(h, Lc, B, pcg, nullptr);
+    for (int i = 0; i < iters && s == TOMO_OK; ++i) s = iteration(h, Lc, B, kind, nullptr);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->work, &graph);
     const long long nodes = h->launches - before;
@@ -352,7 +372,7 @@ tomo_status build_graph(tomo_handle* h, int B, int iters, bool pcg) {
     if (e != cudaSuccess) return TOMO_ECUDA;
     h->graph.B = B;
     h->graph.iters = iters;
-    h->graph.mode = (int)pcg;
+    h->graph.mode = kind;
     h->graph.nodes = nodes;
     return TOMO_OK;
 }
@@ -809,12 +829,14 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
     }
     CK(cg_init_scalars(L, B, h->nparts, h->init_part, o.tol, o.warm_start, h->st));
     const bool pcg = o.precond && h->d_M32;
-    if (pcg) {
+    const int kind = o.method == TOMO_METHOD_MINRES ? kIterMINRES : (pcg ? kIterPCG : kIterCG);
+    if (kind != kIterCG) {
+        // the first row-forward pass reads these with zero coefficients
         CK(cudaMemsetAsync(h->z, 0, sizeof(float) * B * h->N, h->work));
         CK(cudaMemsetAsync(h->w, 0, sizeof(float) * B * h->N, h->work));
     }
     const int chunk = std::max(1, o.check_every);
-    if (!h->timing) TRY(build_graph(h, B, chunk, pcg));
+    if (!h->timing) TRY(build_graph(h, B, chunk, kind));
     long long total_iters = 0;
     std::vector<std::pair<int, int>> marks;
     for (;;) {
@@ -843,7 +865,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             break;
         }
         if (h->timing) {
-            for (int i = 0; i < chunk; ++i) TRY(iteration(h, L, B, pcg, &marks));
+            for (int i = 0; i < chunk; ++i) TRY(iteration(h, L, B, kind, &marks));
         } else {
             CK(cudaGraphLaunch(h->graph.exec, h->work));
             h->launches += h->graph.nodes;
@@ -875,6 +897,14 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
     return TOMO_OK;
 }
 
+tomo_status check_opts(const tomo_solve_opts& o) {
+    if (!(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 || o.check_every < 1) return TOMO_EINVAL;
+    if (o.method != TOMO_METHOD_CG && o.method != TOMO_METHOD_MINRES) return TOMO_EINVAL;
+    if (o.method == TOMO_METHOD_MINRES && o.precond) return TOMO_EINVAL;
+    if (o.warm_start < 0 || o.warm_start > 2) return TOMO_EINVAL;
+    return TOMO_OK;
+}
+
 tomo_solve_opts default_opts() {
     tomo_solve_opts o;
     o.tol = 1e-4;
@@ -883,6 +913,7 @@ tomo_solve_opts default_opts() {
     o.warm_start = 0;
     o.check_every = 32;
     o.precond = 0;
+    o.method = TOMO_METHOD_CG;
     return o;
 }
 
@@ -1028,7 +1059,7 @@ tomo_status tomo_solve(tomo_handle* h, const float* slopes, int batch, const tom
                        float* phase, tomo_frame_info* info) {
     if (!h || !slopes || !zeta || batch < 0) return TOMO_EINVAL;
     tomo_solve_opts o = opts ? *opts : default_opts();
-    if (!(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 || o.check_every < 1) return TOMO_EINVAL;
+    TRY(check_opts(o));
     for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
         const int B = std::min(h->max_batch, batch - f0);
         TRY(solve_chunk(h, slopes + (size_t)f0 * h->N, B, o, zeta + (size_t)f0 * h->N,
@@ -1041,7 +1072,7 @@ tomo_status tomo_solve_r0(tomo_handle* h, const float* slopes, int batch, const 
                           const tomo_solve_opts* opts, float* zeta, float* phase, tomo_frame_info* info) {
     if (!h || !slopes || !zeta || !r0 || batch < 0) return TOMO_EINVAL;
     tomo_solve_opts o = opts ? *opts : default_opts();
-    if (!(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 || o.check_every < 1) return TOMO_EINVAL;
+    TRY(check_opts(o));
     // von Karman covariances scale as r0^{-5/3} (B(0) = c_v (L0 / r0)^{5/3})
     std::vector<double> c(batch);
     for (int f = 0; f < batch; ++f) {

@@ -106,6 +106,27 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
             T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
             *dst = (T)pn;
         }
+    } else if (cgm && cg.mode == 3) {
+        const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+            const size_t i = vbase + e;
+            const int rc = rowcol[e];
+            float re = vr[i];
+            const float pn = re + beta * vp[i];
+            const float apn = vw[i] + beta * vAp[i];
+            if (alpha != 0.f) {
+                vx[i] += alpha * pn;
+                re -= alpha * apn;
+                vr[i] = re;
+            }
+            vp[i] = pn;
+            vAp[i] = apn;
+            rr += (double)re * re;
+            const int row = rc >> 16, col = rc & 0xffff;
+            T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
+            *dst = (T)re;
+        }
     } else if (cgm) {
         const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
 #pragma unroll 4
@@ -565,7 +586,8 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
     const TIn cs = (TIn)fs.x;
     const TIn nv = (TIn)(noise_var[pp] * fs.y);
     const bool cgm = cg.p != nullptr;
-    const float* __restrict__ vr = cg.r;
+    // second partner of the partial sums: r (CG, PCG) or the direction's A p (MINRES)
+    const float* __restrict__ vr = cg.mode == 3 ? cg.Ap : cg.r;
     const int* __restrict__ rowcol = mt.rowcol;
     double acc = 0.0, acc_r = 0.0, acc_a = 0.0;
 #pragma unroll 4
@@ -722,6 +744,7 @@ __global__ void k_cg_init_scalars(int B, int nparts, const double* __restrict__ 
     s.gamma = 0.0;
     s.fresh = 1;
     s.pad_ = 0;
+    s.delta = 0.0;
     st[f] = s;
 }
 
@@ -821,6 +844,59 @@ __global__ void k_pcg_scalars(int B, int NP, const double* __restrict__ rr_part,
 cudaError_t pcg_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_M,
                         const double* dot_A, FrameState* st) {
     k_pcg_scalars<<<(B + 127) / 128, 128, 0, L.stream>>>(B, NP, rr_part, dot_M, dot_A, st);
+    count(L);
+    return cudaGetLastError();
+}
+
+// One thread per frame.  rr_part: r^T r of the residual the row-forward pass
+// produced (r_{k+1}); dot_part: r^T w, Ap^T w, w^T w with w = A r_{k+1} and
+// Ap the direction's product used in that update.  Conjugate residuals:
+// p_{k+1} = r_{k+1} + beta p_k, A p_{k+1} = w + beta A p_k, alpha = r^T A r / |A p|^2;
+// for symmetric positive (semi)definite A these are the MINRES iterates
+// (each x_k minimises the residual norm over the Krylov space).
+__global__ void k_mr_scalars(int B, int NP, const double* __restrict__ rr_part, const double* __restrict__ dot_part,
+                             FrameState* st) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= B || !st[f].active) return;
+    double rr = 0.0, rho = 0.0, apw = 0.0, ww = 0.0;
+    for (int i = 0; i < NP; ++i) {
+        rr += rr_part[(size_t)f * NP + i];
+        const double* d = dot_part + ((size_t)f * NP + i) * 3;
+        rho += d[0];
+        apw += d[1];
+        ww += d[2];
+    }
+    FrameState s = st[f];
+    s.rr = rr;
+    s.relres = sqrt(rr / s.snorm2);
+    if (rr <= s.tol2) {
+        s.active = 0;
+        s.status = 0;
+        st[f] = s;
+        return;
+    }
+    double beta = 0.0, apap = ww;
+    if (!s.fresh) {
+        beta = rho / s.gamma;
+        apap = ww + 2.0 * beta * apw + beta * beta * s.delta;
+    }
+    if (!(rho > 0.0) || !(apap > 0.0) || !isfinite(rho) || !isfinite(apap) || !isfinite(rr)) {
+        s.active = 0;
+        s.status = 2;  // TOMO_FRAME_BREAKDOWN
+        st[f] = s;
+        return;
+    }
+    s.alpha = rho / apap;
+    s.beta = beta;
+    s.gamma = rho;
+    s.delta = apap;
+    s.fresh = 0;
+    s.iters += 1;
+    st[f] = s;
+}
+
+cudaError_t mr_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_part, FrameState* st) {
+    k_mr_scalars<<<(B + 127) / 128, 128, 0, L.stream>>>(B, NP, rr_part, dot_part, st);
     count(L);
     return cudaGetLastError();
 }

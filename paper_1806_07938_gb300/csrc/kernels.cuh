@@ -35,9 +35,10 @@ struct FrameState {
     int active;      // 1 while CG runs on this frame
     int status;      // TOMO_FRAME_*
     int refinements; // restarts from the true residual
-    double gamma;    // PCG: r^T M^{-1} r of the previous iteration
-    int fresh;       // PCG: 1 on the first iteration after a (re)start
+    double gamma;    // PCG: r^T M^{-1} r of the previous iteration; MINRES: r^T A r
+    int fresh;       // PCG, MINRES: 1 on the first iteration after a (re)start
     int pad_;
+    double delta;    // MINRES: (Ap)^T (Ap) of the current direction
 };
 
 // Masked-vector index tables: valid entries of row r are [rowstart[r], rowstart[r+1]),
@@ -63,6 +64,10 @@ cudaError_t init_kernel_attributes();
 //   mode 2 (PCG, Chronopoulos-Gear form): row-forward applies p = z + beta p,
 //                 s = w + beta s, x += alpha p, r -= alpha s and transforms r;
 //                 z = M^{-1} r and w = A z come from the two products of the iteration.
+//   mode 3 (MINRES in conjugate-residual form): row-forward applies
+//                 p = r + beta p, Ap = w + beta Ap, x += alpha p, r -= alpha Ap
+//                 and transforms r; the product gives w = A r and the partial
+//                 sums r^T w, Ap^T w, w^T w.
 struct CgVecs {
     float* x;         // iterate (zeta)
     float* r;         // residual
@@ -72,7 +77,7 @@ struct CgVecs {
     double* dot_part; // [B][NP][3] partial sums xin^T y, r^T y, y^T y of the row-inverse pass
     int mode;
     float* z;         // PCG: M^{-1} r
-    float* w;         // PCG: A z
+    float* w;         // PCG: A z; MINRES: A r
 };
 
 // --- MVM passes ---------------------------------------------------------
@@ -126,6 +131,11 @@ cudaError_t cg_scalars(const Launch& L, int B, int NP, const double* rr_part, co
 // operator pass (xin = z, y = w).
 cudaError_t pcg_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_M,
                         const double* dot_A, FrameState* st);
+// MINRES scalars (conjugate-residual recurrences): rho = r^T A r,
+// beta = rho / rho_old, (Ap)^T(Ap) = w^T w + 2 beta Ap_old^T w + beta^2 (Ap_old)^T(Ap_old),
+// alpha = rho / (Ap)^T(Ap); the convergence test uses r^T r of the row-forward pass.
+cudaError_t mr_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_part,
+                       FrameState* st);
 cudaError_t to_f64(const Launch& L, size_t n, const float* a, double* b);
 cudaError_t true_residual(const Launch& L, int B, int N, int nparts, const float* s,
                           const double* Ax, float* r, double* parts);
@@ -137,8 +147,9 @@ cudaError_t count_active(const Launch& L, int B, const FrameState* st, int* n_ac
 // y [B][nblk][len] <- y - Q^T (Q y) per (frame, block), Q [3][len] orthonormal
 // rows (FP64).  Slopes: nblk = n_gs blocks of len = 2 n_vs; phase: nblk =
 // n_targets blocks of len = n_vphi.  With cg != nullptr (slopes, FP32): also
-// the partial sums xin^T y, r^T y, y^T y of the projected y per plane into
-// cg->dot_part, replacing those of the row-inverse pass that produced y.
+// the partial sums xin^T y, r^T y (Ap^T y in mode 3), y^T y of the projected y
+// per plane into cg->dot_part, replacing those of the row-inverse pass that
+// produced y.
 // Frames with st[f].active == 0 are skipped when st is not null.
 template <typename TV>
 cudaError_t mode_project(const Launch& L, int B, int len, int nblk, const double* Q, const FrameState* st, TV* y,

@@ -90,7 +90,8 @@ cudaError_t mode_project(const Launch& L, int B, int len, int nblk, const double
     if (B <= 0) return cudaSuccess;
     if (cg && (!xin || (len & 1))) return cudaErrorInvalidValue;
     k_mode_project<TV><<<dim3(nblk, B), kModeThreads, 0, L.stream>>>(
-        len, nblk, Q, st, y, cg ? xin : nullptr, cg ? cg->r : nullptr, cg ? cg->dot_part : nullptr);
+        len, nblk, Q, st, y, cg ? xin : nullptr, cg ? (cg->mode == 3 ? cg->Ap : cg->r) : nullptr,
+        cg ? cg->dot_part : nullptr);
     count(L);
     return cudaGetLastError();
 }

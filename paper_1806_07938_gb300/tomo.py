@@ -42,7 +42,8 @@ class tomo_layout_info(ctypes.Structure):
 
 class tomo_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int), ("precond", ctypes.c_int),
+                ("method", ctypes.c_int)]
 
 
 class tomo_frame_info(ctypes.Structure):
@@ -194,9 +195,14 @@ def tomo_apply_cos(h, zeta, phase, batch):
     _check("tomo_apply_cos", lib().tomo_apply_cos(h, _dptr(zeta, torch.float32), _dptr(phase, torch.float32), batch))
 
 
-def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=0, check_every=32, precond=False):
-    """warm_start: 0 cold, 1 zeta holds the guess, 2 the warm-start network's guess."""
-    return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every, int(bool(precond)))
+METHODS = {"cg": 0, "minres": 1}
+
+
+def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=0, check_every=32, precond=False, method="cg"):
+    """warm_start: 0 cold, 1 zeta holds the guess, 2 the warm-start network's guess;
+    method: "cg" or "minres"."""
+    return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every, int(bool(precond)),
+                           METHODS[method])
 
 
 def tomo_solve(h, slopes, batch, opts, zeta, phase=None):

@@ -203,6 +203,49 @@ def test_pcg_golden(T, name):
         assert info["iters"].mean() < infoc["iters"].mean()
 
 
+@pytest.mark.parametrize("method", ["cg", "minres"])
+@pytest.mark.parametrize("k", [1, 4, 10])
+def test_iterates_match_oracle(T, method, k):
+    # the k-th iterate itself, not only the converged solution: max_iter k + 1
+    # passes (the first computes the first product) and no convergence, so the
+    # library returns x_k; the oracle's textbook CG / Lanczos MINRES after k
+    # steps gives the same vector in exact arithmetic (FP32 drift grows with k:
+    # ~1e-7 at k = 4 and ~5e-6 at k = 10 on this system in a CPU FP32 model)
+    cfg = small_cfg(n=8, lgs=True, obstruction=0.2, D=4.8, noise=0.15)
+    A = cov.system_matrix(cfg)
+    s = np.random.default_rng(2).standard_normal((2, A.shape[0]))
+    with Handle(T, cfg, max_batch=2) as H:
+        z, _, info = H.solve(s, tol=1e-12, max_iter=k + 1, max_refine=0, check_every=1, method=method)
+        assert (info["iters"] == k + 1).all() and (info["status"] == 1).all(), info
+        ref = solve.cg if method == "cg" else solve.minres
+        for f in range(2):
+            xk, it = ref(A, s[f], tol=0.0, maxit=k)
+            assert it == k
+            assert relL2(z[f], xk) <= 1e-4, (f, relL2(z[f], xk))
+            # the reported FP64 true residual is that of x_k
+            assert abs(info["relres"][f] - solve.relative_residual(A, s[f], xk)) <= 1e-4 * info["relres"][f]
+
+
+@pytest.mark.parametrize("name", ["ngs8m", "lgs_mid"])
+def test_minres_golden(T, name):
+    # MINRES reaches the same solution (same bounds as CG) in a similar number of products
+    g = golden(name)
+    with Handle(T, g["cfg"], max_batch=4, precond=True) as H:
+        z, phi, info = H.solve(g["s"], tol=1e-5, max_iter=20000, max_refine=3, method="minres")
+        zc, _, infoc = H.solve(g["s"], tol=1e-5, max_iter=20000, max_refine=3)
+        print(name, "MINRES", info, "CG iters", infoc["iters"])
+        assert (info["status"] == 0).all() and (info["relres"] <= 1e-5).all()
+        err = np.linalg.norm(z - g["zeta"], axis=1)
+        bound = info["relres"] * np.linalg.norm(g["s"], axis=1) / min(g["noise_sigma"]) ** 2
+        assert (err <= bound).all()
+        ref = solve.remove_piston(g["phi_interp"].T).T
+        rms = [NM_PER_RAD * np.sqrt(np.mean((solve.remove_piston(phi[f, 0]) - ref[f]) ** 2)) for f in range(4)]
+        assert max(rms) <= 0.1, rms
+        assert info["iters"].mean() < 2 * infoc["iters"].mean()
+        with pytest.raises(T.TomoError):
+            H.solve(g["s"], method="minres", precond=True)       # MINRES takes no preconditioner
+
+
 @pytest.mark.parametrize("n,eps,lgs", [(7, 0.2, True), (12, 0.28, False)])
 def test_apply_precond_matches_oracle(T, n, eps, lgs):
     from oracle import precond
@@ -266,8 +309,9 @@ def test_solve_r0_matches_oracle(T, pcg, noise):
             T.tomo_solve_r0(H.h, sd, 1, np.array([0.1]), T.solve_opts(), zd, noise_scale=np.array([-1.0]))
 
 
-@pytest.mark.parametrize("lgs,pcg", [(False, False), (True, False), (True, True)])
-def test_mode_removal_matches_oracle(T, lgs, pcg):
+@pytest.mark.parametrize("lgs,pcg,method", [(False, False, "cg"), (True, False, "cg"), (True, True, "cg"),
+                                            (True, False, "minres")])
+def test_mode_removal_matches_oracle(T, lgs, pcg, method):
     # split tomography: tip/tilt/focus removed from every WFS and from the
     # estimate; zeta is the minimum-norm solution of M_s A M_s zeta = M_s s
     from oracle import modes
@@ -277,8 +321,8 @@ def test_mode_removal_matches_oracle(T, lgs, pcg):
     s = rng.standard_normal((3, A.shape[0]))
     zs, phis = modes.reconstruct(cfg, s.T, A)
     with Handle(T, cfg, max_batch=2, precond=pcg, mode_removal=True) as H:
-        z, phi, info = H.solve(s, tol=3e-5, max_iter=20000, max_refine=5, precond=pcg)
-        print("modes", info)
+        z, phi, info = H.solve(s, tol=3e-5, max_iter=20000, max_refine=5, precond=pcg, method=method)
+        print("modes", method, info)
         assert (info["status"] == 0).all() and (info["relres"] <= 3e-5).all()
         Ms = modes.slope_removal(cfg)
         assert (modes.relative_residual(cfg, A, s.T, z.T) <= 3.5e-5).all()
@@ -292,7 +336,8 @@ def test_mode_removal_matches_oracle(T, lgs, pcg):
         # blind to the removed modes in the measurements
         Zs = modes.slope_modes(cfg)
         add = np.concatenate([Zs @ rng.standard_normal((3, 3)) for _ in cfg["gs"]]).T
-        z2, phi2, info2 = H.solve(s + 5 * add, tol=3e-5, max_iter=20000, max_refine=5, precond=pcg)
+        z2, phi2, info2 = H.solve(s + 5 * add, tol=3e-5, max_iter=20000, max_refine=5, precond=pcg,
+                                  method=method)
         assert (info2["status"] == 0).all()
         assert relL2(phi2, phi) <= 2e-3
         # without removal the estimate differs

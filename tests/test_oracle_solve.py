@@ -55,3 +55,60 @@ def test_remove_piston():
     out = solve.remove_piston(phi)
     assert np.allclose(out.mean(axis=0), 0.0)
     assert np.allclose(out[:, 0], out[:, 1])
+
+
+def _krylov_min_residual(A, b, k):
+    """argmin ||b - A x|| over span{b, A b, ..., A^{k-1} b}, by brute force."""
+    K = [b / np.linalg.norm(b)]
+    for _ in range(k - 1):
+        K.append(A @ K[-1])
+        K[-1] /= np.linalg.norm(K[-1])
+    Q, _ = np.linalg.qr(np.stack(K, axis=1))
+    y = np.linalg.lstsq(A @ Q, b, rcond=None)[0]
+    return Q @ y
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
+def test_minres_minimises_the_residual_over_the_krylov_space(system, k):
+    # the defining property of MINRES, checked against an explicit Krylov basis
+    _, A, s = system
+    b = s[:, 1]
+    x, it = solve.minres(A, b, tol=0.0, maxit=k)
+    assert it == k
+    ref = _krylov_min_residual(A, b, k)
+    assert np.linalg.norm(x - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_minres_residual_monotone_and_below_cg(system):
+    _, A, s = system
+    b = s[:, 2]
+    prev = np.inf
+    for k in range(1, 40, 3):
+        xm, _ = solve.minres(A, b, tol=0.0, maxit=k)
+        xc, _ = solve.cg(A, b, tol=0.0, maxit=k)
+        rm, rc = np.linalg.norm(b - A @ xm), np.linalg.norm(b - A @ xc)
+        assert rm <= prev * (1 + 1e-12)
+        assert rm <= rc * (1 + 1e-9)
+        prev = rm
+
+
+def test_minres_matches_cholesky_and_scipy(system):
+    import scipy.sparse.linalg as spla
+    _, A, s = system
+    z = solve.solve_cholesky(A, s[:, 0])
+    x, it = solve.minres(A, s[:, 0], tol=1e-12, maxit=20000)
+    assert np.linalg.norm(x - z) / np.linalg.norm(z) < 1e-8
+    # scipy's MINRES after the same number of steps gives the same iterate
+    x12, _ = solve.minres(A, s[:, 0], tol=0.0, maxit=12)
+    xs, _ = spla.minres(A, s[:, 0], rtol=1e-30, maxiter=12)
+    assert np.linalg.norm(x12 - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+def test_minres_singular_consistent_system():
+    # semi-definite, consistent: MINRES from zero converges to the minimum-norm solution
+    rng = np.random.default_rng(8)
+    Q, _ = np.linalg.qr(rng.standard_normal((10, 10)))
+    A = Q @ np.diag(np.r_[np.linspace(1, 4, 8), 0.0, 0.0]) @ Q.T
+    b = A @ rng.standard_normal(10)
+    x, _ = solve.minres(A, b, tol=1e-13, maxit=100)
+    assert np.allclose(x, np.linalg.pinv(A) @ b, atol=1e-10)
