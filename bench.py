@@ -286,8 +286,10 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     F = args.frames
     with torch.cuda.stream(stream):
-        h = tomo.tomo_create(cfg, stream=stream, max_batch=F, precond=True)
+        # fft_P = -1: the library times the candidate FFT sides and keeps the fastest
+        h = tomo.tomo_create(cfg, stream=stream, max_batch=F, precond=True, fft_P=-1)
         layout, sub, ph = tomo.tomo_layout(h)
+        tune_P, tune_ms = tomo.tomo_autotune_result(h)
         s = torch.tensor(tomo.valid_slopes(full, sub), dtype=torch.float32, device="cuda").contiguous()
         z = torch.zeros_like(s)
         phi = torch.empty((F, layout.n_targets, layout.n_vphi), dtype=torch.float32, device="cuda")
@@ -319,52 +321,43 @@ def run_ours(args):
         clk = clocks.stop()
         launches = tomo.tomo_launch_count(h) - launches0
         step_ms = [a.elapsed_time(b) for a, b in evs]
-        # the same frames with the block-circulant preconditioner (reported beside the headline)
-        popts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True)
-        for _ in range(args.warmup):
-            tomo.tomo_solve(h, s, F, popts, z, phi)
-        pevs, pinfos = [], []
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pinfos.append(tomo.tomo_solve(h, s, F, popts, z, phi))
-            e1.record(stream)
-            pevs.append((e0, e1))
-        torch.cuda.synchronize()
-        pms = sum(a.elapsed_time(b) for a, b in pevs)
-        pinfo = pinfos[-1]
-        pcg = {"value": world * F * args.steps / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms / args.steps,
-               "iters_mean": float(pinfo["iters"].mean()), "iters_max": int(pinfo["iters"].max()),
-               "relres_max": float(pinfo["relres"].max()),
-               "all_converged": bool((pinfo["status"] == 0).all() and (pinfo["relres"] <= TOL).all()),
-               "preconditioner": "block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{-1} on the 150 x 150 torus"}
-        # the learned warm start (trained offline on other seeded frames) in front of the same PCG
-        learned = None
-        if not args.no_learned:
-            l0, l1 = train_warm_start(tomo, torch, h, cfg, layout, sub, seed=2000 + rank)
-            lopts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True,
-                                    warm_start=2)
+        def variant(vopts, **extra):
+            """The same frames with other solver options: W warm-up + K timed steps."""
             for _ in range(args.warmup):
-                tomo.tomo_solve(h, s, F, lopts, z, phi)
-            levs, linfos = [], []
+                tomo.tomo_solve(h, s, F, vopts, z, phi)
+            vevs, vinfos = [], []
             for _ in range(args.steps):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                linfos.append(tomo.tomo_solve(h, s, F, lopts, z, phi))
+                vinfos.append(tomo.tomo_solve(h, s, F, vopts, z, phi))
                 e1.record(stream)
-                levs.append((e0, e1))
+                vevs.append((e0, e1))
             torch.cuda.synchronize()
-            lms = sum(a.elapsed_time(b) for a, b in levs)
-            linfo = linfos[-1]
-            learned = {"value": world * F * args.steps / (lms / 1000.0), "unit": UNIT, "ms_per_step": lms / args.steps,
-                       "iters_mean": float(linfo["iters"].mean()),
-                       "all_converged": bool((linfo["status"] == 0).all() and (linfo["relres"] <= TOL).all()),
-                       "training": {"frames": 256, "steps": 200, "loss_first": l0, "loss_last": l1,
-                                    "network": "3x3 CNN 12-32-32-32-12, FP32, warm start of the PCG"}}
+            vms = sum(a.elapsed_time(b) for a, b in vevs)
+            vi = vinfos[-1]
+            out = {"value": world * F * args.steps / (vms / 1000.0), "unit": UNIT, "ms_per_step": vms / args.steps,
+                   "iters_mean": float(vi["iters"].mean()), "iters_max": int(vi["iters"].max()),
+                   "relres_max": float(vi["relres"].max()),
+                   "all_converged": bool((vi["status"] == 0).all() and (vi["relres"] <= TOL).all())}
+            out.update(extra)
+            return out
+
+        # the same frames with the block-circulant preconditioner, and with MINRES (reported beside the headline)
+        pcg = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True),
+                      preconditioner=f"block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{{-1}} on the "
+                                     f"{layout.P} x {layout.P} torus")
+        minres = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=32, method="minres"),
+                         method="MINRES in conjugate-residual form, unpreconditioned (as the paper ran it)")
+        # the learned warm start (trained offline on other seeded frames) in front of the same PCG
+        learned = None
+        if not args.no_learned:
+            l0, l1 = train_warm_start(tomo, torch, h, cfg, layout, sub, seed=2000 + rank)
+            learned = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True,
+                                              warm_start=2),
+                              training={"frames": 256, "steps": 200, "loss_first": l0, "loss_last": l1,
+                                        "network": "3x3 CNN 12-32-32-32-12, FP32, warm start of the PCG"})
         total_ms = sum(step_ms)
         if dist:
             t = torch.tensor([total_ms], device="cuda")
@@ -426,10 +419,11 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames_per_gpu": F, "N": layout.N, "P": layout.P,
                        "Pcos": layout.Pcos, "n_new": layout.n_new,
+                       "fft_P_autotune": {str(int(p)): round(float(t), 4) for p, t in zip(tune_P, tune_ms)},
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "pcg": pcg, "learned_pcg": learned,
+            "pcg": pcg, "minres": minres, "learned_pcg": learned,
             "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                       "relres_max": float(info["relres"].max()), "all_converged": ok,
                       "refinements_max": int(info["refinements"].max()),

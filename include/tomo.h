@@ -92,7 +92,8 @@ typedef struct {
     int n_targets;         /* target directions (>= 1)                            */
     const double* target_x;    /* [n_targets] beta_x [rad]                        */
     const double* target_y;    /* [n_targets] beta_y [rad]                        */
-    int fft_P;             /* padded FFT side for Sigma_ss, 0 = smallest valid    */
+    int fft_P;             /* padded FFT side for Sigma_ss, 0 = smallest valid,
+                              < 0 = autotuned (see tomo_autotune_result)          */
     int fft_Pcos;          /* padded FFT side for Sigma_phi_s, 0 = smallest valid */
     int max_batch;         /* frames per call the workspaces are sized for        */
     int precond;           /* 1: also build the block-circulant preconditioner    */
@@ -160,6 +161,17 @@ typedef struct tomo_handle tomo_handle;
  * altitudes, fractions that are not positive, or an FFT side too small
  * (P >= 2n - 1, Pcos >= n' + n - 1) or with a prime factor above 7. */
 tomo_status tomo_create(const tomo_config* cfg, void* cuda_stream, tomo_handle** out);
+
+/* FFT-side autotuning (no counterpart in the paper, which takes any
+ * P >= 2n - 1, Sec. 2.E).  With cfg.fft_P < 0, tomo_create times the FP32
+ * Sigma_ss product (three passes, on min(max_batch, 64) frames) for every even
+ * side P in [2n - 1, 1.25 (2n - 1)] whose prime factors are <= 7 (at most six
+ * sides, smallest first) and keeps the fastest; the product is exact for any
+ * such P, so the choice changes speed, not results.  This call returns the
+ * sides tried and their mean times in ms (-1: the side could not run) into
+ * sides[capacity] and ms[capacity] (either may be NULL); *count receives the
+ * number of sides (0 when the handle was not autotuned). */
+tomo_status tomo_autotune_result(const tomo_handle* h, int* sides, double* ms, int capacity, int* count);
 
 /* Sizes and, if the pointers are non-NULL, host copies of the subaperture
  * mask (n*n bytes) and phase-point mask ((n+1)*(n+1) bytes). */

@@ -94,6 +94,10 @@ struct tomo_handle {
     double* d_Qs = nullptr;
     double* d_Qp = nullptr;
     float* s_proj = nullptr;           // M_s s of the current chunk
+    // FFT-side autotuning (cfg.fft_P < 0): candidate sides and their measured
+    // Sigma_ss product times [ms] (negative: the side could not run)
+    std::vector<int> tune_P;
+    std::vector<double> tune_ms;
     int* d_iidx = nullptr;
     float* d_iw = nullptr;
     // workspaces
@@ -398,6 +402,91 @@ tomo_status validate(const tomo_config* c) {
     return TOMO_OK;
 }
 
+// Picks the Sigma_ss FFT side P by timing the FP32 product (three passes) on
+// min(max_batch, 64) frames for every even P in [2n - 1, 1.25 (2n - 1)] with
+// radices 2..7 (at most 6 sides).  The product's run time does not depend on
+// the values, so the spectra are zeros here; the chosen side's real spectra
+// are built afterwards.  Needs the mask tables and the noise variances.
+tomo_status autotune_side(tomo_handle* h) {
+    const int n = h->n, pmin = 2 * n - 1;
+    const int pmax = (int)std::ceil(1.25 * pmin);
+    h->tune_P.clear();
+    h->tune_ms.clear();
+    for (int P = pmin + (pmin & 1); P <= pmax && h->tune_P.size() < 6; P += 2) {
+        FftPlan pl;
+        if (make_plan(P, &pl)) h->tune_P.push_back(P);
+    }
+    if (h->tune_P.empty()) h->tune_P.push_back(smallest_fft_side(pmin));
+    const int B = std::min(h->max_batch, 64);
+    const int Pmax = *std::max_element(h->tune_P.begin(), h->tune_P.end());
+    const size_t nhmax = Pmax / 2 + 1;
+    float *x = nullptr, *y = nullptr;
+    float2 *X1 = nullptr, *Y1 = nullptr, *K = nullptr, *tw = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(x); cudaFree(y); cudaFree(X1); cudaFree(Y1); cudaFree(K); cudaFree(tw);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    const size_t nK = (size_t)(h->NP * (h->NP + 1) / 2) * nhmax * Pmax;
+    const size_t nX = (size_t)B * h->NP * nhmax * n;
+    if (cudaMalloc(&x, sizeof(float) * B * h->N) != cudaSuccess || cudaMalloc(&y, sizeof(float) * B * h->N) ||
+        cudaMalloc(&X1, sizeof(float2) * nX) || cudaMalloc(&Y1, sizeof(float2) * nX) ||
+        cudaMalloc(&K, sizeof(float2) * nK) || cudaMalloc(&tw, sizeof(float2) * Pmax) ||
+        cudaEventCreate(&e0) || cudaEventCreate(&e1)) {
+        cleanup();
+        cudaGetLastError();
+        return TOMO_ENOMEM;
+    }
+    Launch L{h->stream, nullptr};
+    double best = 0.0;
+    int bestP = 0;
+    cudaError_t err = cudaMemsetAsync(x, 0, sizeof(float) * B * h->N, h->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(K, 0, sizeof(float2) * nK, h->stream);
+    for (int P : h->tune_P) {
+        FftPlan pl;
+        make_plan(P, &pl);
+        const MvmGeom g{n, n, h->NP, h->NP, P / 2 + 1, pl};
+        const auto t = twiddles<float2>(P);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(tw, t.data(), sizeof(float2) * P, cudaMemcpyHostToDevice, h->stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+        if (err != cudaSuccess) break;
+        auto product = [&]() -> cudaError_t {
+            cudaError_t e = rows_fwd<float, float>(L, g, h->mt, B, x, nullptr, nullptr, X1, tw);
+            if (e == cudaSuccess) e = cols_mul<float>(L, g, B, nullptr, X1, Y1, K, tw, true);
+            if (e == cudaSuccess)
+                e = rows_inv_masked<float, float>(L, g, h->mt, B, nullptr, Y1, x, h->d_noise_var, nullptr, y, nullptr,
+                                                  tw);
+            return e;
+        };
+        double ms = -1.0;
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = product();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = product();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t_ms = 0.f;
+        if (e == cudaSuccess && cudaEventElapsedTime(&t_ms, e0, e1) == cudaSuccess) ms = t_ms / 5.0;
+        if (e == cudaErrorInvalidValue) {
+            cudaGetLastError();       // a launch configuration this side cannot use: skip it
+        } else if (e != cudaSuccess) {
+            err = e;
+            break;
+        }
+        h->tune_ms.push_back(ms);
+        if (ms > 0 && (bestP == 0 || ms < best)) { best = ms; bestP = P; }
+    }
+    cleanup();
+    if (err != cudaSuccess) {
+        std::fprintf(stderr, "tomo: FFT-side autotuning failed: %s\n", cudaGetErrorString(err));
+        return TOMO_ECUDA;
+    }
+    if (bestP == 0) return TOMO_EINVAL;
+    h->P = bestP;
+    return TOMO_OK;
+}
+
 tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     h->stream = static_cast<cudaStream_t>(stream);
     CK(init_kernel_attributes());
@@ -497,15 +586,6 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     h->m = h->all_ngs ? n + 1 : (int)std::ceil((double)n / gmin - 1e-9) + 1;
     h->cos_layers = h->all_ngs ? 1 : h->n_layers;
 
-    // --- FFT sides and plans ----------------------------------------------------------
-    h->P = c->fft_P > 0 ? c->fft_P : smallest_fft_side(2 * n - 1);
-    h->Pc = c->fft_Pcos > 0 ? c->fft_Pcos : smallest_fft_side(h->m + n - 1);
-    if (h->P < 2 * n - 1 || (h->P & 1) || h->Pc < h->m + n - 1 || (h->Pc & 1)) return TOMO_EINVAL;
-    if (!make_plan(h->P, &h->plan) || !make_plan(h->Pc, &h->planc)) return TOMO_EINVAL;
-    if (h->cos_layers > 16) return TOMO_ERANGE;
-    h->g_ss = MvmGeom{n, n, h->NP, h->NP, h->P / 2 + 1, h->plan};
-    h->g_os = MvmGeom{n, h->m, h->NP, h->cos_layers, h->Pc / 2 + 1, h->planc};
-
     // --- device tables -------------------------------------------------------------
     TRY(dalloc(h, &h->d_rowstart, n + 1));
     TRY(dalloc(h, &h->d_col, h->n_vs));
@@ -521,6 +601,16 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     for (int p = 0; p < h->NP; ++p) nvar[p] = c->gs[p / 2].noise_sigma * c->gs[p / 2].noise_sigma;
     TRY(dalloc(h, &h->d_noise_var, h->NP));
     TRY(upload(h, nvar.data(), h->d_noise_var, sizeof(double) * h->NP));
+
+    // --- FFT sides and plans ----------------------------------------------------------
+    if (c->fft_P < 0) TRY(autotune_side(h));
+    h->P = c->fft_P > 0 ? c->fft_P : (c->fft_P < 0 ? h->P : smallest_fft_side(2 * n - 1));
+    h->Pc = c->fft_Pcos > 0 ? c->fft_Pcos : smallest_fft_side(h->m + n - 1);
+    if (h->P < 2 * n - 1 || (h->P & 1) || h->Pc < h->m + n - 1 || (h->Pc & 1)) return TOMO_EINVAL;
+    if (!make_plan(h->P, &h->plan) || !make_plan(h->Pc, &h->planc)) return TOMO_EINVAL;
+    if (h->cos_layers > 16) return TOMO_ERANGE;
+    h->g_ss = MvmGeom{n, n, h->NP, h->NP, h->P / 2 + 1, h->plan};
+    h->g_os = MvmGeom{n, h->m, h->NP, h->cos_layers, h->Pc / 2 + 1, h->planc};
     auto tw32 = twiddles<float2>(h->P);
     auto tw64 = twiddles<double2>(h->P);
     auto twc32 = twiddles<float2>(h->Pc);
@@ -1004,6 +1094,16 @@ tomo_status tomo_create(const tomo_config* cfg, void* cuda_stream, tomo_handle**
         return s;
     }
     *out = h;
+    return TOMO_OK;
+}
+
+tomo_status tomo_autotune_result(const tomo_handle* h, int* sides, double* ms, int capacity, int* count) {
+    if (!h || !count || capacity < 0) return TOMO_EINVAL;
+    *count = (int)h->tune_P.size();
+    for (int i = 0; i < *count && i < capacity; ++i) {
+        if (sides) sides[i] = h->tune_P[i];
+        if (ms) ms[i] = i < (int)h->tune_ms.size() ? h->tune_ms[i] : -1.0;
+    }
     return TOMO_OK;
 }
 

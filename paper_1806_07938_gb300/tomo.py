@@ -56,7 +56,7 @@ FRAME_INFO_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("s
 
 EXPORTS = ("tomo_create", "tomo_layout", "tomo_apply_css", "tomo_apply_css_noalloc", "tomo_apply_css_f64",
            "tomo_apply_cos",
-           "tomo_solve", "tomo_solve_r0", "tomo_solve_host", "tomo_launch_count", "tomo_set_kernel_timing",
+           "tomo_solve", "tomo_solve_r0", "tomo_solve_host", "tomo_autotune_result", "tomo_launch_count", "tomo_set_kernel_timing",
            "tomo_apply_precond", "tomo_ws_init", "tomo_ws_param_count", "tomo_ws_set_params", "tomo_ws_get_params", "tomo_ws_apply",
            "tomo_ws_gradient", "tomo_ws_train_step",
            "tomo_get_kernel_timing", "tomo_destroy", "tomo_strerror")
@@ -90,6 +90,7 @@ def lib(path=None):
     L.tomo_apply_cos.argtypes = [vp, vp, vp, i]
     L.tomo_solve.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_solve_host.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
+    L.tomo_autotune_result.argtypes = [vp, vp, vp, i, ctypes.POINTER(i)]
     L.tomo_solve_r0.argtypes = [vp, vp, i, vp, vp, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_launch_count.argtypes = [vp]
     L.tomo_launch_count.restype = ctypes.c_longlong
@@ -161,6 +162,18 @@ def tomo_create(cfg, stream=None, max_batch=1, fft_P=0, fft_Pcos=0, precond=Fals
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
     _check("tomo_create", L.tomo_create(ctypes.byref(c), s, ctypes.byref(h)))
     return h
+
+
+def tomo_autotune_result(h):
+    """(sides, ms) the FFT-side autotuner timed; empty when not autotuned."""
+    cnt = ctypes.c_int()
+    _check("tomo_autotune_result", lib().tomo_autotune_result(h, None, None, 0, ctypes.byref(cnt)))
+    sides = np.zeros(cnt.value, np.int32)
+    ms = np.zeros(cnt.value, np.float64)
+    if cnt.value:
+        _check("tomo_autotune_result", lib().tomo_autotune_result(
+            h, ctypes.c_void_p(sides.ctypes.data), ctypes.c_void_p(ms.ctypes.data), cnt.value, ctypes.byref(cnt)))
+    return sides, ms
 
 
 def tomo_layout(h):

@@ -122,6 +122,22 @@ def test_css_small_live(T, n, eps, lgs, P):
         assert relL2(H.css(x, f64=True), x @ A.T) <= 1e-11
 
 
+def test_autotuned_fft_side(T):
+    # fft_P < 0: the side is chosen by timing every candidate; results do not change
+    g = golden("ngs8m")                                       # n = 20: 2n - 1 = 39
+    with Handle(T, g["cfg"], max_batch=4, fft_P=-1) as H:
+        sides, ms = T.tomo_autotune_result(H.h)
+        print("autotune", sides, ms)
+        assert list(sides) == [40, 42, 48]                    # even, 7-smooth, <= 1.25 * 39
+        assert (ms > 0).all()
+        assert H.info.P == sides[np.argmin(ms)]
+        assert relL2(H.css(g["x"]), g["y"]) <= 1e-5
+        z, _, info = H.solve(g["s"], tol=1e-4)
+        assert (info["status"] == 0).all()
+    with Handle(T, g["cfg"], max_batch=4) as H:
+        assert len(T.tomo_autotune_result(H.h)[0]) == 0 and H.info.P == 40
+
+
 def test_css_zero_and_empty(T):
     cfg = small_cfg(n=6, lgs=True)
     with Handle(T, cfg, max_batch=2) as H:
