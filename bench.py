@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=FRAMES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="time only the headline plain-CG solve (no PCG, MINRES, closed-loop or learned variants)")
     return ap.parse_args()
 
 
@@ -278,6 +280,7 @@ def run_ours(args):
     import torch
 
     from paper_1806_07938_gb300 import tomo
+    from paper_1806_07938_gb300 import workloads as W
 
     world, rank, local, dist = dist_setup(True)
     torch.cuda.set_device(local)
@@ -345,19 +348,51 @@ def run_ours(args):
             return out
 
         # the same frames with the block-circulant preconditioner, and with MINRES (reported beside the headline)
-        pcg = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True),
-                      preconditioner=f"block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{{-1}} on the "
-                                     f"{layout.P} x {layout.P} torus")
-        minres = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=32, method="minres"),
-                         method="MINRES in conjugate-residual form, unpreconditioned (as the paper ran it)")
-        # the learned warm start (trained offline on other seeded frames) in front of the same PCG
-        learned = None
-        if not args.no_learned:
-            l0, l1 = train_warm_start(tomo, torch, h, cfg, layout, sub, seed=2000 + rank)
-            learned = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True,
-                                              warm_start=2),
-                              training={"frames": 256, "steps": 200, "loss_first": l0, "loss_last": l1,
-                                        "network": "3x3 CNN 12-32-32-32-12, FP32, warm start of the PCG"})
+        pcg = minres = warm_prev = learned = None
+        if not args.no_variants:
+            pcg = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True),
+                          preconditioner=f"block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{{-1}} on the "
+                                         f"{layout.P} x {layout.P} torus")
+            minres = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=32, method="minres"),
+                             method="MINRES in conjugate-residual form, unpreconditioned (as the paper ran it)")
+            # closed-loop operation (Sec. 5): frozen-flow sequences at 1 kHz, each step
+            # warm-started from the previous step's solution, PCG
+            seq, _ = W.slope_sequence_parallel(cfg, F, args.warmup + args.steps + 1, seed=3000 + rank, dt=1e-3)
+            seq_s = [torch.tensor(tomo.valid_slopes(seq[t], sub), dtype=torch.float32, device="cuda").contiguous()
+                     for t in range(seq.shape[0])]
+            wopts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True, warm_start=1)
+            zs = torch.zeros_like(s)
+            cold = tomo.tomo_solve(h, seq_s[0], F, tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3,
+                                                                   check_every=16, precond=True), zs, phi)
+            for t in range(1, args.warmup + 1):
+                tomo.tomo_solve(h, seq_s[t], F, wopts, zs, phi)
+            wevs, winfos = [], []
+            for t in range(args.warmup + 1, args.warmup + args.steps + 1):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                winfos.append(tomo.tomo_solve(h, seq_s[t], F, wopts, zs, phi))
+                e1.record(stream)
+                wevs.append((e0, e1))
+            torch.cuda.synchronize()
+            wms = sum(a.elapsed_time(b) for a, b in wevs)
+            wi = winfos[-1]
+            warm_prev = {"value": world * F * args.steps / (wms / 1000.0), "unit": UNIT, "ms_per_step": wms / args.steps,
+                         "iters_mean": float(np.mean([w["iters"].mean() for w in winfos])),
+                         "cold_iters_mean": float(cold["iters"].mean()),
+                         "relres_max": float(max(w["relres"].max() for w in winfos)),
+                         "all_converged": bool(all((w["status"] == 0).all() and (w["relres"] <= TOL).all()
+                                                   for w in winfos)),
+                         "workload": ("the same system on frozen-flow sequences (synthetic 9-layer wind, 8-25 m/s, "
+                                      "1 ms steps), each step's PCG started from the previous step's zeta")}
+            # the learned warm start (trained offline on other seeded frames) in front of the same PCG
+            if not args.no_learned:
+                l0, l1 = train_warm_start(tomo, torch, h, cfg, layout, sub, seed=2000 + rank)
+                learned = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True,
+                                                  warm_start=2),
+                                  training={"frames": 256, "steps": 200, "loss_first": l0, "loss_last": l1,
+                                            "network": "3x3 CNN 12-32-32-32-12, FP32, warm start of the PCG"})
         total_ms = sum(step_ms)
         if dist:
             t = torch.tensor([total_ms], device="cuda")
@@ -423,7 +458,7 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "pcg": pcg, "minres": minres, "learned_pcg": learned,
+            "pcg": pcg, "minres": minres, "learned_pcg": learned, "pcg_warm_previous": warm_prev,
             "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                       "relres_max": float(info["relres"].max()), "all_converged": ok,
                       "refinements_max": int(info["refinements"].max()),

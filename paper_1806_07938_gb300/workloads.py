@@ -29,6 +29,11 @@ noiseless slopes is added.  Every screen and noise draw comes from numpy's
 counter-based Philox generator keyed by (seed, frame, layer), so a frame does
 not depend on how many frames are generated with it.
 
+Time sequences (``slope_sequence``): frozen flow, each layer's screen moves
+rigidly with its wind vector, so step t samples the screen at x - v t dt; the
+screens of a sequence are drawn once, the noise anew at every step.  The wind
+profile is synthetic as well (the paper gives none).
+
 Slopes are returned on the full n x n subaperture grid,
 ``[frame][gs][x|y][i][j]``; callers select the valid subapertures with the mask
 of the side they exercise.
@@ -42,6 +47,9 @@ ARCSEC = math.pi / (180.0 * 3600.0)
 
 NINE_LAYER_H = [0.0, 500.0, 1000.0, 2000.0, 4000.0, 8000.0, 12000.0, 16000.0, 20000.0]
 NINE_LAYER_FRAC = [0.40, 0.12, 0.10, 0.09, 0.08, 0.07, 0.06, 0.05, 0.03]
+# synthetic frozen-flow wind per layer: speed [m/s], direction [rad]
+NINE_LAYER_WIND = [(10.0, 0.0), (8.0, 0.8), (9.0, 1.6), (12.0, 2.4), (15.0, 3.2), (20.0, 4.0), (25.0, 4.8),
+                   (18.0, 5.6), (12.0, 0.4)]
 
 
 def ring(n_gs, radius, height, phase0=0.0):
@@ -98,11 +106,9 @@ def bilinear(scr, pix, x, y):
             + (1 - fx) * fy * scr[iy1, ix] + fx * fy * scr[iy1, ix1])
 
 
-def _clean_frame(cfg, seed, f, screen_px, grids):
-    """Noiseless slopes [gs][x|y][n][n] of frame ``f``."""
-    n, D = cfg["n"], cfg["D"]
-    pix = D / n / 2.0
-    (cx, cy), (vx, vy), (hx, hy) = grids
+def _screens(cfg, seed, f, screen_px):
+    """The layer screens of frame (or sequence) ``f``: [(h, frac, screen)]."""
+    pix = cfg["D"] / cfg["n"] / 2.0
     screens = []
     rng = _rng(seed, f, 0)
     for k in range(0, len(cfg["layers"]), 2):
@@ -111,17 +117,32 @@ def _clean_frame(cfg, seed, f, screen_px, grids):
         a, b = screen_pair(rng, screen_px, pix, cfg["r0"], cfg["L0"])
         for idx, (h, frac) in enumerate(pair):
             screens.append((h, frac, a if idx == 0 else b))
+    return screens
+
+
+def _clean_frame(cfg, seed, f, screen_px, grids, shifts=None):
+    """Noiseless slopes [gs][x|y][n][n] of frame ``f``; shifts[k] = (dx, dy)
+    moves layer k's screen by that many metres (frozen flow)."""
+    return _sample(cfg, _screens(cfg, seed, f, screen_px), grids, shifts)
+
+
+def _sample(cfg, screens, grids, shifts=None):
+    n, D = cfg["n"], cfg["D"]
+    pix = D / n / 2.0
+    (cx, cy), (vx, vy), (hx, hy) = grids
     out = np.zeros((len(cfg["gs"]), 2, n, n))
     for g, (ax, ay, H) in enumerate(cfg["gs"]):
         pc = np.zeros_like(cx)
         pv = np.zeros_like(vx)
         ph = np.zeros_like(hx)
-        for (h, frac, scr) in screens:
+        for k, (h, frac, scr) in enumerate(screens):
             gam = 1.0 if H == 0.0 else 1.0 - h / H
             s = math.sqrt(frac)                   # layer amplitude: r0_k^{-5/6} = frac^{1/2} r0^{-5/6}
-            pc += s * bilinear(scr, pix, gam * cx + h * ax, gam * cy + h * ay)
-            pv += s * bilinear(scr, pix, gam * vx + h * ax, gam * vy + h * ay)
-            ph += s * bilinear(scr, pix, gam * hx + h * ax, gam * hy + h * ay)
+            ox = h * ax - (shifts[k][0] if shifts is not None else 0.0)
+            oy = h * ay - (shifts[k][1] if shifts is not None else 0.0)
+            pc += s * bilinear(scr, pix, gam * cx + ox, gam * cy + oy)
+            pv += s * bilinear(scr, pix, gam * vx + ox, gam * vy + oy)
+            ph += s * bilinear(scr, pix, gam * hx + ox, gam * hy + oy)
         # edge means by the trapezoid rule over corner, midpoint, corner
         right = (pc[:-1, 1:] + 2.0 * pv[:, 1:] + pc[1:, 1:]) / 4.0
         left = (pc[:-1, :-1] + 2.0 * pv[:, :-1] + pc[1:, :-1]) / 4.0
@@ -161,6 +182,67 @@ def slope_frames(cfg, n_frames, seed=0, screen_px=512, first=0):
         rng = _rng(seed, f, 999)
         noisy[i] += sigma[:, None, None, None] * rng.standard_normal((n_gs, 2, n, n))
     return noisy, sigma
+
+
+def _grids(cfg):
+    n, D = cfg["n"], cfg["D"]
+    d = D / n
+    e = (np.arange(n + 1) - n / 2.0) * d
+    m = (np.arange(n) + 0.5 - n / 2.0) * d
+    cy, cx = np.meshgrid(e, e, indexing="ij")
+    vy, vx = np.meshgrid(m, e, indexing="ij")
+    hy, hx = np.meshgrid(e, m, indexing="ij")
+    return ((cx, cy), (vx, vy), (hx, hy))
+
+
+def wind(cfg):
+    """Per-layer wind vectors [(vx, vy)] in m/s (the synthetic profile for 9
+    layers, 10 m/s along +x otherwise)."""
+    if len(cfg["layers"]) == len(NINE_LAYER_WIND):
+        return [(v * math.cos(a), v * math.sin(a)) for v, a in NINE_LAYER_WIND]
+    return [(10.0, 0.0)] * len(cfg["layers"])
+
+
+def slope_sequence(cfg, n_seq, n_steps, seed=0, dt=1e-3, screen_px=512, first=0):
+    """Frozen-flow time sequences: noisy slopes [step][sequence][gs][x|y][n][n]
+    of sequences first .. first+n_seq-1 at times t dt, t = 0 .. n_steps-1, and the
+    per-GS noise sigma (the same calibration as slope_frames).  Sequence j uses
+    the screens of frame j of ``seed``; step t's noise is drawn from stream
+    1000 + t of that frame."""
+    grids = _grids(cfg)
+    n_gs = len(cfg["gs"])
+    calib = np.stack([_clean_frame(cfg, seed, f, screen_px, grids) for f in range(N_CALIBRATION_FRAMES)])
+    sigma = cfg["noise_frac"] * np.sqrt(np.mean(calib ** 2, axis=(0, 2, 3, 4)))
+    v = wind(cfg)
+    n = cfg["n"]
+    out = np.zeros((n_steps, n_seq, n_gs, 2, n, n))
+    for j in range(n_seq):
+        screens = _screens(cfg, seed, first + j, screen_px)
+        for t in range(n_steps):
+            shifts = [(vx * t * dt, vy * t * dt) for vx, vy in v]
+            out[t, j] = _sample(cfg, screens, grids, shifts)
+            rng = _rng(seed, first + j, 1000 + t)
+            out[t, j] += sigma[:, None, None, None] * rng.standard_normal((n_gs, 2, n, n))
+    return out, sigma
+
+
+def _sequence_job(args):
+    cfg, n_seq, n_steps, seed, dt, first = args
+    return slope_sequence(cfg, n_seq, n_steps, seed=seed, dt=dt, first=first)
+
+
+def slope_sequence_parallel(cfg, n_seq, n_steps, seed=0, dt=1e-3, workers=None, chunk=4):
+    """slope_sequence on a pool of `spawn` worker processes (identical result)."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    workers = workers or min(32, os.cpu_count() or 1)
+    jobs = [(cfg, min(chunk, n_seq - a), n_steps, seed, dt, a) for a in range(0, n_seq, chunk)]
+    if workers <= 1 or len(jobs) <= 1:
+        return slope_sequence(cfg, n_seq, n_steps, seed=seed, dt=dt)
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_sequence_job, jobs))
+    return np.concatenate([p[0] for p in parts], axis=1), parts[0][1]
 
 
 def _frames_job(args):
