@@ -348,13 +348,32 @@ def run_ours(args):
             return out
 
         # the same frames with the block-circulant preconditioner, and with MINRES (reported beside the headline)
-        pcg = minres = warm_prev = learned = None
+        pcg = minres = warm_prev = learned = single = None
         if not args.no_variants:
             pcg = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True),
                           preconditioner=f"block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{{-1}} on the "
                                          f"{layout.P} x {layout.P} torus")
             minres = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=32, method="minres"),
                              method="MINRES in conjugate-residual form, unpreconditioned (as the paper ran it)")
+            # single-frame latency: one frame per solve (the row passes then run
+            # one block per group of 16 row pairs), PCG
+            one_opts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True)
+            for _ in range(args.warmup):
+                tomo.tomo_solve(h, s[:1], 1, one_opts, z[:1], phi[:1])
+            oevs, oinfo = [], None
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                oinfo = tomo.tomo_solve(h, s[:1], 1, one_opts, z[:1], phi[:1])
+                e1.record(stream)
+                oevs.append((e0, e1))
+            torch.cuda.synchronize()
+            oms = [a.elapsed_time(b) for a, b in oevs]
+            single = {"ms_per_frame": statistics.median(oms), "iters": int(oinfo["iters"][0]),
+                      "relres": float(oinfo["relres"][0]),
+                      "note": "latency of one frame solved alone (PCG, tol 1e-4, projection included)"}
             # closed-loop operation (Sec. 5): frozen-flow sequences at 1 kHz, each step
             # warm-started from the previous step's solution, PCG
             seq, _ = W.slope_sequence_parallel(cfg, F, args.warmup + args.steps + 1, seed=3000 + rank, dt=1e-3)
@@ -459,6 +478,7 @@ def run_ours(args):
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "pcg": pcg, "minres": minres, "learned_pcg": learned, "pcg_warm_previous": warm_prev,
+            "single_frame_pcg": single,
             "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                       "relres_max": float(info["relres"].max()), "all_converged": ok,
                       "refinements_max": int(info["refinements"].max()),

@@ -59,6 +59,8 @@ struct tomo_handle {
     // configuration
     int n = 0, n_gs = 0, NP = 0, n_vs = 0, N = 0, n_vphi = 0, n_layers = 0, n_targets = 0;
     int P = 0, Pc = 0, m = 0, cos_layers = 0, max_batch = 0;
+    int rg = 1;                        // row groups per plane of the row passes (partial-sum layout)
+    int block_slots = 456;             // SMs x resident blocks of the row passes
     double D = 0, obstruction = 0, d = 0, r0 = 0, L0 = 0;
     bool all_ngs = true;
     std::vector<double> tx, ty;
@@ -218,15 +220,21 @@ tomo_status upload(tomo_handle* h, const void* host, void* dev, size_t bytes) {
 
 Launch launch_of(tomo_handle* h) { return Launch{h->stream, &h->launches}; }
 
+// Row groups of the row passes for a batch of B frames: one block per plane
+// while the batch fills a wave of the GPU, one block per group of row pairs
+// when it does not (small batches, single-frame latency).
+int rg_for(const tomo_handle* h, int B) { return (long long)h->NP * B >= h->block_slots ? 1 : h->rg; }
+
 // Sigma_ss + noise on FP32 vectors; with cg != nullptr, one CG product (see rows_fwd).
 tomo_status apply_ss32(tomo_handle* h, const Launch& L, const float* x, float* y, int B, const FrameState* st,
                        const CgVecs* cg, const double2* fscale = nullptr) {
-    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, x, cg, st, h->X1, h->d_tw32)));
+    const int rg = rg_for(h, B);
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, x, cg, st, h->X1, h->d_tw32, rg)));
     CK((cols_mul<float>(L, h->g_ss, B, st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
     const float* xin = cg ? cg->p : x;
     float* yout = cg ? cg->Ap : y;
     CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, st, h->Y1, xin, h->d_noise_var, fscale, yout, cg,
-                                      h->d_tw32)));
+                                      h->d_tw32, rg)));
     return TOMO_OK;
 }
 
@@ -236,16 +244,17 @@ CgVecs cg_vecs(tomo_handle* h, int mode, double* dots) {
 
 tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double* y, int B,
                        const double2* fscale = nullptr) {
-    CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1d, h->d_tw64)));
+    const int rg = rg_for(h, B);
+    CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1d, h->d_tw64, rg)));
     CK((cols_mul<double>(L, h->g_ss, B, nullptr, h->X1d, h->Y1d, h->d_K64, h->d_tw64, false)));
     CK((rows_inv_masked<double, double>(L, h->g_ss, h->mt, B, nullptr, h->Y1d, x, h->d_noise_var, fscale, y,
-                                        nullptr, h->d_tw64)));
+                                        nullptr, h->d_tw64, rg)));
     return TOMO_OK;
 }
 
 tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi, int B,
                      const double2* fscale = nullptr) {
-    CK((rows_fwd<float, float>(L, h->g_os, h->mt, B, z, nullptr, nullptr, h->Xc, h->d_twc32)));
+    CK((rows_fwd<float, float>(L, h->g_os, h->mt, B, z, nullptr, nullptr, h->Xc, h->d_twc32, rg_for(h, B))));
     const size_t kc_stride = (size_t)h->g_os.nh * h->Pc * h->cos_layers * h->NP;
     for (int t = 0; t < h->n_targets; ++t) {
         CK((cols_mul<float>(L, h->g_os, B, nullptr, h->Xc, h->Yc, h->d_Kc32 + t * kc_stride, h->d_twc32, false)));
@@ -285,54 +294,55 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, int kind, std::vec
         return TOMO_OK;
     };
     // slot encoding: pair (start event * 8 + kernel class, end event)
+    const int rg = rg_for(h, B);
     TRY(mark(0));
     if (kind == kIterMINRES) {
         const CgVecs cg = cg_vecs(h, 3, h->dot_part);
-        CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32)));
+        CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32, rg)));
         TRY(mark(0));
         CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
         TRY(mark(1));
         CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->r, h->d_noise_var, h->d_fscale,
-                                          h->w, &cg, h->d_tw32)));
-        if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, h->d_Qs, h->st, h->w, h->r, &cg));
+                                          h->w, &cg, h->d_tw32, rg)));
+        if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, rg, h->d_Qs, h->st, h->w, h->r, &cg));
         TRY(mark(2));
-        CK(mr_scalars(L, B, h->NP, h->rr_part, h->dot_part, h->st));
+        CK(mr_scalars(L, B, h->NP * rg, h->rr_part, h->dot_part, h->st));
         TRY(mark(3));
         return TOMO_OK;
     }
     if (kind == kIterCG) {
         const CgVecs cg = cg_vecs(h, 1, h->dot_part);
-        CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32)));
+        CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32, rg)));
         TRY(mark(0));
         CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
         TRY(mark(1));
         CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->d_fscale,
-                                          h->Ap, &cg, h->d_tw32)));
-        if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, h->d_Qs, h->st, h->Ap, h->p, &cg));
+                                          h->Ap, &cg, h->d_tw32, rg)));
+        if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, rg, h->d_Qs, h->st, h->Ap, h->p, &cg));
         TRY(mark(2));
-        CK(cg_scalars(L, B, h->NP, h->rr_part, h->dot_part, h->st));
+        CK(cg_scalars(L, B, h->NP * rg, h->rr_part, h->dot_part, h->st));
         TRY(mark(3));
         return TOMO_OK;
     }
     const CgVecs cgM = cg_vecs(h, 2, h->dot_part_M);
     const CgVecs cgA = cg_vecs(h, 2, h->dot_part);
-    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cgM, h->st, h->X1, h->d_tw32)));
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cgM, h->st, h->X1, h->d_tw32, rg)));
     TRY(mark(0));
     CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_M32, h->d_tw32, true)));
     TRY(mark(1));
     CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->r, h->d_zero_var, h->d_fscale_pre,
-                                      h->z, &cgM, h->d_tw32)));
-    if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, h->d_Qs, h->st, h->z, h->r, &cgM));
+                                      h->z, &cgM, h->d_tw32, rg)));
+    if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, rg, h->d_Qs, h->st, h->z, h->r, &cgM));
     TRY(mark(2));
-    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, h->z, nullptr, h->st, h->X1, h->d_tw32)));
+    CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, h->z, nullptr, h->st, h->X1, h->d_tw32, rg)));
     TRY(mark(0));
     CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
     TRY(mark(1));
     CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->z, h->d_noise_var, h->d_fscale,
-                                      h->w, &cgA, h->d_tw32)));
-    if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, h->d_Qs, h->st, h->w, h->z, &cgA));
+                                      h->w, &cgA, h->d_tw32, rg)));
+    if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, rg, h->d_Qs, h->st, h->w, h->z, &cgA));
     TRY(mark(2));
-    CK(pcg_scalars(L, B, h->NP, h->rr_part, h->dot_part_M, h->dot_part, h->st));
+    CK(pcg_scalars(L, B, h->NP * rg, h->rr_part, h->dot_part_M, h->dot_part, h->st));
     TRY(mark(3));
     return TOMO_OK;
 }
@@ -526,6 +536,13 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     h->n_vs = (int)col.size();
     if (h->n_vs == 0) return TOMO_EINVAL;
     h->N = h->NP * h->n_vs;
+    h->rg = row_groups(n);
+    {
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        h->block_slots = sms * TOMO_MIN_BLOCKS;
+    }
     h->phase_mask.assign((size_t)(n + 1) * (n + 1), 0);
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j)
@@ -760,11 +777,11 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     TRY(dalloc(h, &h->yd, B * h->N));
     TRY(dalloc(h, &h->st, B));
     h->nparts = std::max(1, std::min(64, (h->N + 4095) / 4096));
-    TRY(dalloc(h, &h->dot_part, B * h->NP * 3));
-    TRY(dalloc(h, &h->dot_part_M, B * h->NP * 3));
+    TRY(dalloc(h, &h->dot_part, B * h->NP * h->rg * 3));
+    TRY(dalloc(h, &h->dot_part_M, B * h->NP * h->rg * 3));
     TRY(dalloc(h, &h->z, B * h->N));
     TRY(dalloc(h, &h->w, B * h->N));
-    TRY(dalloc(h, &h->rr_part, B * h->NP));
+    TRY(dalloc(h, &h->rr_part, B * h->NP * h->rg));
     TRY(dalloc(h, &h->res_part, B * h->nparts));
     TRY(dalloc(h, &h->init_part, B * 2 * h->nparts));
     TRY(dalloc(h, &h->d_nactive, 1));
@@ -882,23 +899,23 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
     if (h->modes) {
         // right-hand side M_s s
         CK(cudaMemcpyAsync(h->s_proj, s, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
-        CK(mode_project<float>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->s_proj, nullptr, nullptr));
+        CK(mode_project<float>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->s_proj, nullptr, nullptr));
         s = h->s_proj;
     }
     // A x0 for a warm start x0 (projected first under mode removal)
     auto start_from_x = [&]() -> tomo_status {
-        if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->x, nullptr, nullptr));
+        if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->x, nullptr, nullptr));
         TRY(apply_ss32(h, L, h->x, h->Ap, B, nullptr, nullptr, h->d_fscale));
-        if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->Ap, nullptr, nullptr));
+        if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->Ap, nullptr, nullptr));
         CK(cg_init(L, B, h->N, h->nparts, s, h->Ap, h->x, h->r, h->p, h->Ap, h->init_part));
         return TOMO_OK;
     };
     // FP64 true residual r = s - A x (M_s s - M_s A M_s x under mode removal)
     auto true_res = [&](int max_refine) -> tomo_status {
         CK(to_f64(L, (size_t)B * h->N, h->x, h->xd));
-        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->xd, nullptr, nullptr));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->xd, nullptr, nullptr));
         TRY(apply_ss64(h, L, h->xd, h->yd, B, h->d_fscale));
-        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->yd, nullptr, nullptr));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->yd, nullptr, nullptr));
         CK(true_residual(L, B, h->N, h->nparts, s, h->yd, h->r, h->res_part));
         CK(true_residual_finalize(L, B, h->nparts, h->res_part, o.tol, max_refine, h->st));
         return TOMO_OK;
@@ -962,12 +979,12 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         }
         total_iters += chunk;
     }
-    if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->d_Qs, nullptr, h->x, nullptr, nullptr));
+    if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->x, nullptr, nullptr));
     CK(cudaMemcpyAsync(zeta, h->x, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
     if (phase) {
         TRY(apply_os(h, L, h->x, phase, B, h->d_fscale));
         if (h->modes)
-            CK(mode_project<float>(L, B, h->n_vphi, h->n_targets, h->d_Qp, nullptr, phase, nullptr, nullptr));
+            CK(mode_project<float>(L, B, h->n_vphi, h->n_targets, 1, h->d_Qp, nullptr, phase, nullptr, nullptr));
     }
     CK(cudaEventRecord(h->ev_out, h->work));
     CK(cudaStreamWaitEvent(h->stream, h->ev_out, 0));

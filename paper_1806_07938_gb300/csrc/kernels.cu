@@ -29,6 +29,8 @@ inline void count(const Launch& L) {
     if (L.counter) ++*L.counter;
 }
 
+static_assert(kRowPairsPerBlock == kWarps * kFftGroup, "a row group is one round of the block's warps");
+
 int g_max_smem = 48 * 1024;   // raised by init_kernel_attributes()
 
 template <typename T>
@@ -63,8 +65,12 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kWarps];
     const int P = g.plan.P, n = g.n, nh = g.nh, RS = row_stride(P);
-    const int npair = (n + 1) / 2;
-    const int ngrp = (npair + G - 1) / G;
+    // this block's row group: row pairs [pb, pb + npl) of the plane (all of
+    // them when the plane is one block)
+    const int ppb = gridDim.z == 1 ? (n + 1) / 2 : kRowPairsPerBlock;
+    const int pb = blockIdx.z * ppb;
+    const int npl = min(ppb, (n + 1) / 2 - pb);
+    const int ngrp = (npl + G - 1) / G;
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* scr = tw + P;                                // generic-path scratch, one per warp
     C* F = scr + (Fused<PC>::ok ? 0 : kWarps * P);  // [ngrp * G][RS]
@@ -73,6 +79,8 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
     for (int i = threadIdx.x; i < ngrp * G * RS; i += blockDim.x) F[i] = cmk<C>(0, 0);
+    // valid entries of rows [2 pb, 2 (pb + npl)) (row-major: a contiguous range)
+    const int e0 = mt.rowstart[2 * pb], e1 = mt.rowstart[min(2 * (pb + npl), n)];
     __syncthreads();
     // sweep over the plane's valid entries (W_s^T scatter), with the CG update
     const size_t vbase = ((size_t)f * g.NPin + q) * mt.n_vs;
@@ -88,7 +96,7 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
     if (cgm && cg.mode == 1) {
         const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
 #pragma unroll 4
-        for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
             const size_t i = vbase + e;
             const int rc = rowcol[e];
             const float pe = vp[i];
@@ -103,13 +111,13 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
             vp[i] = pn;
             rr += (double)re * re;
             const int row = rc >> 16, col = rc & 0xffff;
-            T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
+            T* dst = reinterpret_cast<T*>(F + ((row >> 1) - pb) * RS + col) + (row & 1);
             *dst = (T)pn;
         }
     } else if (cgm && cg.mode == 3) {
         const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
 #pragma unroll 4
-        for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
             const size_t i = vbase + e;
             const int rc = rowcol[e];
             float re = vr[i];
@@ -124,13 +132,13 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
             vAp[i] = apn;
             rr += (double)re * re;
             const int row = rc >> 16, col = rc & 0xffff;
-            T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
+            T* dst = reinterpret_cast<T*>(F + ((row >> 1) - pb) * RS + col) + (row & 1);
             *dst = (T)re;
         }
     } else if (cgm) {
         const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
 #pragma unroll 4
-        for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
             const size_t i = vbase + e;
             const int rc = rowcol[e];
             const float pn = vz[i] + beta * vp[i];
@@ -145,15 +153,15 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
             vAp[i] = sn;
             rr += (double)re * re;
             const int row = rc >> 16, col = rc & 0xffff;
-            T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
+            T* dst = reinterpret_cast<T*>(F + ((row >> 1) - pb) * RS + col) + (row & 1);
             *dst = (T)re;
         }
     } else {
 #pragma unroll 4
-        for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
             const int rc = rowcol[e];
             const int row = rc >> 16, col = rc & 0xffff;
-            T* dst = reinterpret_cast<T*>(F + (row >> 1) * RS + col) + (row & 1);
+            T* dst = reinterpret_cast<T*>(F + ((row >> 1) - pb) * RS + col) + (row & 1);
             *dst = (T)__ldg(x + vbase + e);
         }
     }
@@ -162,7 +170,7 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
         fft_g<PC, C, true>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane, n, P);
     if (cgm) {
         const double t = block_sum<T>(rr, red);
-        if (threadIdx.x == 0) cg.rr_part[(size_t)f * g.NPin + q] = t;
+        if (threadIdx.x == 0) cg.rr_part[((size_t)f * g.NPin + q) * gridDim.z + blockIdx.z] = t;
     }
     __syncthreads();
     // unpack the two real spectra of each pair, A = (Z_k + conj Z_{P-k})/2,
@@ -170,9 +178,10 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
     C* out = X1T + ((size_t)f * g.NPin + q) * nh * n;
     for (int k = warp; k < nh; k += kWarps) {
         const int kc = k == 0 ? 0 : P - k;
-        for (int j = lane; j < npair; j += 32) {
-            const C zk = F[j * RS + k];
-            const C zc = cconj(F[j * RS + kc]);
+        for (int jl = lane; jl < npl; jl += 32) {
+            const int j = pb + jl;
+            const C zk = F[jl * RS + k];
+            const C zc = cconj(F[jl * RS + kc]);
             const C dd = csub(zk, zc);
             out[(size_t)k * n + 2 * j] = cscale(cadd(zk, zc), (T)0.5);
             if (2 * j + 1 < n) out[(size_t)k * n + 2 * j + 1] = cmk<C>((T)0.5 * dd.y, (T)-0.5 * dd.x);
@@ -190,11 +199,13 @@ size_t rows_smem(const MvmGeom& g, int nrows) {
 
 template <typename T, typename TIn>
 cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const TIn* x, const CgVecs* cg,
-                     const FrameState* st, cplx_t<T>* X1T, const cplx_t<T>* tw) {
+                     const FrameState* st, cplx_t<T>* X1T, const cplx_t<T>* tw, int rg) {
     const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
-    const size_t smem = rows_smem<T>(g, g.n);
+    if (rg != 1 && rg != row_groups(g.n)) return cudaErrorInvalidValue;
+    const size_t smem = rows_smem<T>(g, rg == 1 ? g.n : 2 * kRowPairsPerBlock);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
-#define TOMO_L(PC) k_rows_fwd<T, TIn, PC><<<dim3(g.NPin, B), kThreads, smem, L.stream>>>(g, mt, x, cgv, st, X1T, tw)
+#define TOMO_L(PC)                                                                                      \
+    k_rows_fwd<T, TIn, PC><<<dim3(g.NPin, B, rg), kThreads, smem, L.stream>>>(g, mt, x, cgv, st, X1T, tw)
     TOMO_DISPATCH_P(g.plan.P, TOMO_L)
 #undef TOMO_L
     count(L);
@@ -526,9 +537,10 @@ __device__ __forceinline__ void put_row_pair(C* F, int RS, int P, int j, int k, 
     }
 }
 
+// Pairs [pb, pb + npair) of the plane go to F rows [0, npair).
 template <typename C>
-__device__ __forceinline__ void load_row_pairs(const C* __restrict__ src, int m, int P, int nh, int RS, C* F) {
-    const int npair = (m + 1) / 2;
+__device__ __forceinline__ void load_row_pairs(const C* __restrict__ src, int m, int P, int nh, int RS, C* F,
+                                               int pb, int npair) {
     const int total = nh * npair;
     constexpr int U = 4;
     for (int i0 = threadIdx.x; i0 < total; i0 += U * blockDim.x) {
@@ -537,9 +549,9 @@ __device__ __forceinline__ void load_row_pairs(const C* __restrict__ src, int m,
         for (int u = 0; u < U; ++u) {
             const int i = i0 + u * blockDim.x;
             if (i < total) {
-                const int k = i / npair, j = i - k * npair;
-                a[u] = __ldg(src + (size_t)k * m + 2 * j);
-                b[u] = 2 * j + 1 < m ? __ldg(src + (size_t)k * m + 2 * j + 1) : cmk<C>(0, 0);
+                const int k = i / npair, j = i - k * npair, r = 2 * (pb + j);
+                a[u] = __ldg(src + (size_t)k * m + r);
+                b[u] = r + 1 < m ? __ldg(src + (size_t)k * m + r + 1) : cmk<C>(0, 0);
             }
         }
 #pragma unroll
@@ -564,7 +576,11 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[kWarps];
     const int P = g.plan.P, m = g.m, nh = g.nh, RS = row_stride(P);
-    const int npair = (m + 1) / 2;
+    // this block's row group: output row pairs [pb, pb + npair) of the plane
+    // (all of them when the plane is one block)
+    const int ppb = gridDim.z == 1 ? (m + 1) / 2 : kRowPairsPerBlock;
+    const int pb = blockIdx.z * ppb;
+    const int npair = min(ppb, (m + 1) / 2 - pb);
     const int ngrp = (npair + G - 1) / G;
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* scr = tw + P;
@@ -575,7 +591,7 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
     for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
     if (npair < ngrp * G)
         for (int i = threadIdx.x; i < (ngrp * G - npair) * RS; i += blockDim.x) F[npair * RS + i] = cmk<C>(0, 0);
-    load_row_pairs<C>(Y1T + ((size_t)f * g.NPout + pp) * nh * m, m, P, nh, RS, F);
+    load_row_pairs<C>(Y1T + ((size_t)f * g.NPout + pp) * nh * m, m, P, nh, RS, F, pb, npair);
     __syncthreads();
     for (int gi = warp; gi < ngrp; gi += kWarps)
         fft_g<PC, C, false>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane, P, m);
@@ -590,13 +606,14 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
     const float* __restrict__ vr = cg.mode == 3 ? cg.Ap : cg.r;
     const int* __restrict__ rowcol = mt.rowcol;
     double acc = 0.0, acc_r = 0.0, acc_a = 0.0;
+    const int e0 = mt.rowstart[2 * pb], e1 = mt.rowstart[min(2 * (pb + npair), m)];
 #pragma unroll 4
-    for (int e = threadIdx.x; e < mt.n_vs; e += blockDim.x) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int rc = rowcol[e];
         const int row = rc >> 16, col = rc & 0xffff;
         const TIn xi = __ldg(xin + vbase + e);
         const float ri = cgm ? __ldg(vr + vbase + e) : 0.f;
-        const T v = reinterpret_cast<const T*>(F + (row >> 1) * RS + col)[row & 1];
+        const T v = reinterpret_cast<const T*>(F + ((row >> 1) - pb) * RS + col)[row & 1];
         const TIn out = cs * (TIn)v + nv * xi;
         y[vbase + e] = out;
         if (cgm) {
@@ -606,7 +623,7 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
         }
     }
     if (cgm) {
-        double* dp = cg.dot_part + ((size_t)f * g.NPout + pp) * 3;
+        double* dp = cg.dot_part + (((size_t)f * g.NPout + pp) * gridDim.z + blockIdx.z) * 3;
         const double s0 = block_sum<T>(acc, red);
         if (threadIdx.x == 0) dp[0] = s0;
         const double s1 = block_sum<T>(acc_r, red);
@@ -619,13 +636,14 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
 template <typename T, typename TIn>
 cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const FrameState* st,
                             const cplx_t<T>* Y1T, const TIn* xin, const double* noise_var, const double2* fscale,
-                            TIn* y, const CgVecs* cg, const cplx_t<T>* tw) {
+                            TIn* y, const CgVecs* cg, const cplx_t<T>* tw, int rg) {
     const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
-    const size_t smem = rows_smem<T>(g, g.m);
+    if (rg != 1 && rg != row_groups(g.m)) return cudaErrorInvalidValue;
+    const size_t smem = rows_smem<T>(g, rg == 1 ? g.m : 2 * kRowPairsPerBlock);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
-#define TOMO_L(PC)                                                                                   \
-    k_rows_inv_masked<T, TIn, PC><<<dim3(g.NPout, B), kThreads, smem, L.stream>>>(g, mt, st, Y1T, xin, \
-                                                                                  noise_var, fscale, y, cgv, tw)
+#define TOMO_L(PC)                                                                                \
+    k_rows_inv_masked<T, TIn, PC><<<dim3(g.NPout, B, rg), kThreads, smem, L.stream>>>(               \
+        g, mt, st, Y1T, xin, noise_var, fscale, y, cgv, tw)
     TOMO_DISPATCH_P(g.plan.P, TOMO_L)
 #undef TOMO_L
     count(L);
@@ -1369,19 +1387,19 @@ cudaError_t init_kernel_attributes() {
 
 // explicit instantiations
 template cudaError_t rows_fwd<float, float>(const Launch&, const MvmGeom&, const MaskTables&, int, const float*,
-                                            const CgVecs*, const FrameState*, float2*, const float2*);
+                                            const CgVecs*, const FrameState*, float2*, const float2*, int);
 template cudaError_t rows_fwd<double, double>(const Launch&, const MvmGeom&, const MaskTables&, int, const double*,
-                                              const CgVecs*, const FrameState*, double2*, const double2*);
+                                              const CgVecs*, const FrameState*, double2*, const double2*, int);
 template cudaError_t cols_mul<float>(const Launch&, const MvmGeom&, int, const FrameState*, const float2*, float2*,
                                      const float2*, const float2*, bool);
 template cudaError_t cols_mul<double>(const Launch&, const MvmGeom&, int, const FrameState*, const double2*, double2*,
                                       const double2*, const double2*, bool);
 template cudaError_t rows_inv_masked<float, float>(const Launch&, const MvmGeom&, const MaskTables&, int,
                                                    const FrameState*, const float2*, const float*, const double*,
-                                                   const double2*, float*, const CgVecs*, const float2*);
+                                                   const double2*, float*, const CgVecs*, const float2*, int);
 template cudaError_t rows_inv_masked<double, double>(const Launch&, const MvmGeom&, const MaskTables&, int,
                                                      const FrameState*, const double2*, const double*, const double*,
-                                                     const double2*, double*, const CgVecs*, const double2*);
+                                                     const double2*, double*, const CgVecs*, const double2*, int);
 template cudaError_t rows_inv_dense<float>(const Launch&, const MvmGeom&, int, const float2*, float*, const float2*);
 
 }  // namespace tomo

@@ -15,6 +15,15 @@ constexpr int kThreads = 32 * kWarps;
 #define TOMO_MIN_BLOCKS 3                  // resident blocks per SM the FFT kernels are compiled for
 #endif
 
+// Row passes: one block transforms up to kRowPairsPerBlock row pairs of one
+// plane of one frame (one pair per sequence, kFftGroup sequences per warp), so
+// a plane of n rows is split over row_groups(n) blocks.  Partial sums of the
+// row passes are stored per (frame, plane, row group).
+constexpr int kRowPairsPerBlock = 16;
+__host__ __device__ constexpr int row_groups(int nrows) {
+    return ((nrows + 1) / 2 + kRowPairsPerBlock - 1) / kRowPairsPerBlock;
+}
+
 // Geometry of one FFT-based 2RBT product y = T x (Sec. 2.E): inputs are NPin
 // masked planes on an n x n grid, outputs NPout planes on an m x m grid, both
 // embedded in a P x P periodic grid (P >= m + n - 1); half spectrum nh = P/2+1.
@@ -73,8 +82,8 @@ struct CgVecs {
     float* r;         // residual
     float* p;         // search direction
     float* Ap;        // CG: A p of the previous iteration; PCG: s, the recurrence for A p
-    double* rr_part;  // [B][NP] partial sums of r^T r after the update
-    double* dot_part; // [B][NP][3] partial sums xin^T y, r^T y, y^T y of the row-inverse pass
+    double* rr_part;  // [B][NP][row groups] partial sums of r^T r after the update
+    double* dot_part; // [B][NP][row groups][3] partial sums xin^T y, r^T y, y^T y of the row-inverse pass
     int mode;
     float* z;         // PCG: M^{-1} r
     float* w;         // PCG: A z; MINRES: A r
@@ -85,10 +94,12 @@ struct CgVecs {
 // CG mode (cg != nullptr; x ignored): first applies the previous iteration's
 // update x += alpha p, r -= alpha Ap, forms p = r + beta p, accumulates r^T r
 // of the updated residual, and transforms p.
+// rg: 1 (one block per plane) or row_groups(g.n) (one block per row group);
+// the partial sums are stored per (frame, plane, row group) accordingly.
 template <typename T, typename TIn>
 cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B,
                      const TIn* x, const CgVecs* cg, const FrameState* st,
-                     cplx_t<T>* X1T, const cplx_t<T>* tw);
+                     cplx_t<T>* X1T, const cplx_t<T>* tw, int rg = 1);
 
 // Column pass: forward column FFT of the NPin planes, per-frequency block
 // multiply by K [nh][NPin][P][NPout] (herm = false) or by the Hermitian
@@ -108,7 +119,7 @@ template <typename T, typename TIn>
 cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B,
                             const FrameState* st, const cplx_t<T>* Y1T, const TIn* xin,
                             const double* noise_var, const double2* fscale, TIn* y, const CgVecs* cg,
-                            const cplx_t<T>* tw);
+                            const cplx_t<T>* tw, int rg = 1);
 
 // Row-inverse pass to a dense m x m output per plane: Yd [B][NPout][m][m].
 template <typename T>
@@ -120,6 +131,8 @@ cudaError_t cg_init(const Launch& L, int B, int N, int nparts, const float* s, c
                     float* x, float* r, float* p, float* Ap, double* parts);
 cudaError_t cg_init_scalars(const Launch& L, int B, int nparts, const double* parts, double tol,
                             int warm, FrameState* st);
+// The scalar kernels take NP = the number of partial-sum entries per frame
+// (planes x row groups).
 // Per-frame scalars after an iteration: convergence test on the updated
 // residual, alpha, and beta of the next iteration from
 // r_new^T r_new = r^T r - 2 alpha r^T Ap + alpha^2 Ap^T Ap (Chronopoulos & Gear).
@@ -151,9 +164,10 @@ cudaError_t count_active(const Launch& L, int B, const FrameState* st, int* n_ac
 // per plane into cg->dot_part, replacing those of the row-inverse pass that
 // produced y.
 // Frames with st[f].active == 0 are skipped when st is not null.
+// rg: row groups per plane of the partial-sum layout.
 template <typename TV>
-cudaError_t mode_project(const Launch& L, int B, int len, int nblk, const double* Q, const FrameState* st, TV* y,
-                         const float* xin, const CgVecs* cg);
+cudaError_t mode_project(const Launch& L, int B, int len, int nblk, int rg, const double* Q, const FrameState* st,
+                         TV* y, const float* xin, const CgVecs* cg);
 
 // --- setup ------------------------------------------------------------------
 struct VkParams {

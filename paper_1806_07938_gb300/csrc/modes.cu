@@ -44,7 +44,7 @@ __device__ __forceinline__ void block_sums(double (&v)[V], double (*red)[kModeTh
 // (the x- and y-slope planes), stored like the row-inverse pass stores them.
 template <typename TV>
 __global__ void __launch_bounds__(kModeThreads)
-k_mode_project(int len, int nblk, const double* __restrict__ Q, const FrameState* st, TV* __restrict__ y,
+k_mode_project(int len, int nblk, int rg, const double* __restrict__ Q, const FrameState* st, TV* __restrict__ y,
                const float* __restrict__ xin, const float* __restrict__ r, double* __restrict__ dots) {
     __shared__ double red[6][kModeThreads / 32];
     const int blk = blockIdx.x, f = blockIdx.y;
@@ -74,10 +74,12 @@ k_mode_project(int len, int nblk, const double* __restrict__ Q, const FrameState
         }
     }
     if (dots) {
+        // the row passes store partial sums per (plane, row group): the projected
+        // sums go to row group 0, the other groups' entries are cleared
         block_sums<6>(d, red);
-        if (threadIdx.x < 6) {
-            const int plane = 2 * blk + threadIdx.x / 3;
-            dots[((size_t)f * 2 * nblk + plane) * 3 + threadIdx.x % 3] = d[threadIdx.x];
+        for (int i = threadIdx.x; i < 6 * rg; i += blockDim.x) {
+            const int plane = 2 * blk + i / (3 * rg), grp = (i / 3) % rg, c = i % 3;
+            dots[(((size_t)f * 2 * nblk + plane) * rg + grp) * 3 + c] = grp == 0 ? d[(i / (3 * rg)) * 3 + c] : 0.0;
         }
     }
 }
@@ -85,20 +87,20 @@ k_mode_project(int len, int nblk, const double* __restrict__ Q, const FrameState
 }  // namespace
 
 template <typename TV>
-cudaError_t mode_project(const Launch& L, int B, int len, int nblk, const double* Q, const FrameState* st, TV* y,
-                         const float* xin, const CgVecs* cg) {
+cudaError_t mode_project(const Launch& L, int B, int len, int nblk, int rg, const double* Q, const FrameState* st,
+                         TV* y, const float* xin, const CgVecs* cg) {
     if (B <= 0) return cudaSuccess;
-    if (cg && (!xin || (len & 1))) return cudaErrorInvalidValue;
+    if (cg && (!xin || (len & 1) || rg < 1)) return cudaErrorInvalidValue;
     k_mode_project<TV><<<dim3(nblk, B), kModeThreads, 0, L.stream>>>(
-        len, nblk, Q, st, y, cg ? xin : nullptr, cg ? (cg->mode == 3 ? cg->Ap : cg->r) : nullptr,
+        len, nblk, rg, Q, st, y, cg ? xin : nullptr, cg ? (cg->mode == 3 ? cg->Ap : cg->r) : nullptr,
         cg ? cg->dot_part : nullptr);
     count(L);
     return cudaGetLastError();
 }
 
-template cudaError_t mode_project<float>(const Launch&, int, int, int, const double*, const FrameState*, float*,
-                                         const float*, const CgVecs*);
-template cudaError_t mode_project<double>(const Launch&, int, int, int, const double*, const FrameState*, double*,
-                                          const float*, const CgVecs*);
+template cudaError_t mode_project<float>(const Launch&, int, int, int, int, const double*, const FrameState*,
+                                         float*, const float*, const CgVecs*);
+template cudaError_t mode_project<double>(const Launch&, int, int, int, int, const double*, const FrameState*,
+                                          double*, const float*, const CgVecs*);
 
 }  // namespace tomo

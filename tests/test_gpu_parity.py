@@ -138,6 +138,25 @@ def test_autotuned_fft_side(T):
         assert len(T.tomo_autotune_result(H.h)[0]) == 0 and H.info.P == 40
 
 
+def test_row_group_split_matches_oracle(T):
+    # n = 36 has 18 row pairs: small batches run the row passes as two blocks
+    # per plane (16 + 2 pairs) and store partial sums per row group
+    cfg = small_cfg(n=36, n_gs=2, lgs=True, obstruction=0.2, D=0.5 * 36, layers=((8000.0, 1.0),), noise=0.2)
+    A = cov.system_matrix(cfg)
+    x = np.random.default_rng(36).standard_normal((3, A.shape[0]))
+    with Handle(T, cfg, max_batch=3) as H:
+        assert relL2(H.css(x), x @ A.T) <= 1e-5
+        assert relL2(H.css(x, f64=True), x @ A.T) <= 1e-11
+        # cond(A) = 4.3e4 and a white right-hand side: FP32 operators floor the
+        # true residual near 6e-5 here, so the solve is checked at 1.5e-4
+        for method in ("cg", "minres"):
+            z, _, info = H.solve(x, tol=1.5e-4, max_iter=20000, max_refine=5, method=method)
+            assert (info["status"] == 0).all() and (info["relres"] <= 1.5e-4).all(), info
+            zs = solve.solve_cholesky(A, x.T).T
+            bound = info["relres"] * np.linalg.norm(x, axis=1) / 0.2 ** 2
+            assert (np.linalg.norm(z - zs, axis=1) <= bound).all()
+
+
 def test_css_zero_and_empty(T):
     cfg = small_cfg(n=6, lgs=True)
     with Handle(T, cfg, max_batch=2) as H:
