@@ -348,7 +348,7 @@ def run_ours(args):
             return out
 
         # the same frames with the block-circulant preconditioner, and with MINRES (reported beside the headline)
-        pcg = minres = warm_prev = learned = single = None
+        pcg = minres = warm_prev = learned = single = direct = None
         if not args.no_variants:
             pcg = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True),
                           preconditioner=f"block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{{-1}} on the "
@@ -374,6 +374,42 @@ def run_ours(args):
             single = {"ms_per_frame": statistics.median(oms), "iters": int(oinfo["iters"][0]),
                       "relres": float(oinfo["relres"][0]),
                       "note": "latency of one frame solved alone (PCG, tol 1e-4, projection included)"}
+            # the explicit reconstructor (the paper's "direct MVM" comparison):
+            # built from n_vphi PCG solves, then applied to the frames as a GEMM
+            R = torch.empty((layout.n_vphi, layout.N), dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rinfo = tomo.tomo_reconstructor(h, 0, tomo.solve_opts(tol=1e-5, max_iter=30000, max_refine=3,
+                                                                  check_every=16, precond=True), R)
+            torch.cuda.synchronize()
+            build_s = time.perf_counter() - t0
+            phiR = torch.empty((F, layout.n_vphi), dtype=torch.float32, device="cuda")
+            for _ in range(args.warmup):
+                tomo.tomo_apply_reconstructor(h, R, s, F, phiR)
+            revs = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tomo.tomo_apply_reconstructor(h, R, s, F, phiR)
+                e1.record(stream)
+                revs.append((e0, e1))
+            torch.cuda.synchronize()
+            rms_ = [a.elapsed_time(b) for a, b in revs]
+            r_ms = statistics.median(rms_)
+            flops_R = 2.0 * F * layout.n_vphi * layout.N
+            bytes_R = 4.0 * layout.n_vphi * layout.N
+            direct = {"value": world * F / (r_ms / 1000.0), "unit": UNIT, "ms_per_step": r_ms,
+                      "build_s": build_s, "build_rows": layout.n_vphi,
+                      "build_iters_mean": float(rinfo["iters"].mean()),
+                      "build_all_converged": bool((rinfo["status"] == 0).all()),
+                      "R_bytes": bytes_R, "gemm_tflops": flops_R / (r_ms / 1000.0) / 1e12,
+                      "gemm_gbs": bytes_R / (r_ms / 1000.0) / 1e9,
+                      "note": "R = Sigma_phi_s A^{-1} (target 0) from PCG solves at 1e-5, applied by the FP32 GEMM; "
+                              "value excludes the build"}
+            del R, phiR
+            torch.cuda.empty_cache()
             # closed-loop operation (Sec. 5): frozen-flow sequences at 1 kHz, each step
             # warm-started from the previous step's solution, PCG
             seq, _ = W.slope_sequence_parallel(cfg, F, args.warmup + args.steps + 1, seed=3000 + rank, dt=1e-3)
@@ -478,7 +514,7 @@ def run_ours(args):
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "pcg": pcg, "minres": minres, "learned_pcg": learned, "pcg_warm_previous": warm_prev,
-            "single_frame_pcg": single,
+            "single_frame_pcg": single, "direct_mvm": direct,
             "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                       "relres_max": float(info["relres"].max()), "all_converged": ok,
                       "refinements_max": int(info["refinements"].max()),

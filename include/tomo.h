@@ -213,6 +213,34 @@ tomo_status tomo_apply_css_f64(tomo_handle* h, const double* x_dev, double* y_de
  * [batch][n_targets][n_vphi] device floats. */
 tomo_status tomo_apply_cos(tomo_handle* h, const float* zeta_dev, float* phase_dev, int batch);
 
+/* The adjoint of tomo_apply_cos: zeta = sum_t W_s Sigma_s_phi_t W_phi^T phi_t,
+ * the exact transpose of the same FP32 operator (for LGS the transposed
+ * bilinear interpolation, then the conjugate-transposed per-frequency
+ * blocks of Eq. ToeplitzLGS; for NGS the transposed Eq. mvm_ps).
+ * phase_dev [batch][n_targets][n_vphi], zeta_dev [batch][N] device floats. */
+tomo_status tomo_apply_cos_adjoint(tomo_handle* h, const float* phase_dev, float* zeta_dev, int batch);
+
+/* The explicit reconstructor of one target (Eq. covBasedReconstructors1):
+ *     R = W_phi Sigma_phi_s W_s^T (W_s (Sigma_ss + Sigma_eta_eta) W_s^T)^{-1},
+ * the matrix a "direct MVM" reconstructor applies (the paper's comparison,
+ * Sec. 4.B).  Row v of R solves the system with the right-hand side
+ * W_s Sigma_s_phi W_phi^T e_v (tomo_apply_cos_adjoint of a unit phase), so
+ * R is built by n_vphi solves, max_batch at a time, with the options in opts
+ * (NULL: tomo_solve's defaults; warm_start must be 0).  R_dev: device
+ * [n_vphi][N] floats; info_host: NULL or [n_vphi] per-row solve outcomes.
+ * TOMO_EINVAL with mode removal (cfg.mode_removal).  Uses the handle's
+ * staging buffers of tomo_solve_host: do not run both at the same time. */
+tomo_status tomo_reconstructor(tomo_handle* h, int target, const tomo_solve_opts* opts, float* R_dev,
+                               tomo_frame_info* info_host);
+
+/* phase[b][v] = sum_j R[v][j] s[b][j]: the direct MVM with an explicit
+ * reconstructor R_dev [rows][N] (e.g. from tomo_reconstructor), FP32,
+ * hand-written tiled GEMM split over N with a fixed summation order.
+ * slopes_dev [batch][N], phase_dev [batch][rows] device floats.  May
+ * allocate a workspace on the first call with a larger batch x rows. */
+tomo_status tomo_apply_reconstructor(tomo_handle* h, const float* R_dev, int rows, const float* slopes_dev,
+                                     int batch, float* phase_dev);
+
 /* Full reconstruction of `batch` frames: CG (FP32 vectors and MVMs, FP64
  * dot products and alpha/beta) on Eq. SAap1, FP64 true residual at exit and
  * restarts from it while it exceeds opts->tol, then the projection of

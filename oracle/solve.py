@@ -102,6 +102,13 @@ def minres(A, s, tol=1e-4, maxit=10000, x0=None):
     return x, it
 
 
+def reconstructor(F, A):
+    """Explicit reconstructor R = F A^{-1} (Eq. covBasedReconstructors1) for the
+    projection F (n_vphi x N) and the SPD system matrix A, by Cholesky
+    (R^T = A^{-1} F^T since A is symmetric)."""
+    return solve_cholesky(A, F.T).T
+
+
 def remove_piston(phi):
     """Subtract the mean over the (valid) phase points; slopes do not see piston."""
     return phi - phi.mean(axis=0, keepdims=True)

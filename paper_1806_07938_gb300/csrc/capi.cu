@@ -96,6 +96,19 @@ struct tomo_handle {
     double* d_Qs = nullptr;
     double* d_Qp = nullptr;
     float* s_proj = nullptr;           // M_s s of the current chunk
+    // adjoint of the projection (built on first use) and the explicit reconstructor
+    int* d_aptr = nullptr;             // transposed bilinear table [layer][m*m + 1]
+    int* d_avi = nullptr;
+    float* d_aw = nullptr;
+    int *d_rowstart_m = nullptr, *d_col_m = nullptr, *d_rowcol_m = nullptr;
+    MaskTables mt_m{};                 // every node of the m x m layer grid
+    MvmGeom g_adj{};
+    bool adj_ready = false;
+    float2* d_Kadj = nullptr;          // [target] conjugate-transposed projection spectra
+    float2 *Xa = nullptr, *Ya = nullptr;
+    float *Yda = nullptr, *za = nullptr;
+    float* gemm_part = nullptr;
+    size_t gemm_part_size = 0;
     // FFT-side autotuning (cfg.fft_P < 0): candidate sides and their measured
     // Sigma_ss product times [ms] (negative: the side could not run)
     std::vector<int> tune_P;
@@ -757,6 +770,48 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         TRY(dalloc(h, &h->d_iw, w.size()));
         TRY(upload(h, idx.data(), h->d_iidx, sizeof(int) * idx.size()));
         TRY(upload(h, w.data(), h->d_iw, sizeof(float) * w.size()));
+        // transposed table for the adjoint: per layer and grid node, the
+        // (phase point, weight) pairs that read it, in phase-point order
+        const int m2 = m * m;
+        std::vector<int> aptr((size_t)L_ * (m2 + 1), 0), avi(idx.size());
+        std::vector<float> aw(idx.size());
+        size_t off = 0;
+        for (int k = 0; k < L_; ++k) {
+            std::vector<int> cnt(m2 + 1, 0);
+            for (int v = 0; v < h->n_vphi; ++v)
+                for (int c = 0; c < 4; ++c) ++cnt[idx[((size_t)k * h->n_vphi + v) * 4 + c] + 1];
+            int* pk = aptr.data() + (size_t)k * (m2 + 1);
+            pk[0] = (int)off;
+            for (int i = 0; i < m2; ++i) pk[i + 1] = pk[i] + cnt[i + 1];
+            std::vector<int> fill(pk, pk + m2);
+            for (int v = 0; v < h->n_vphi; ++v)
+                for (int c = 0; c < 4; ++c) {
+                    const size_t o = ((size_t)k * h->n_vphi + v) * 4 + c;
+                    const int e = fill[idx[o]]++;
+                    avi[e] = v;
+                    aw[e] = w[o];
+                }
+            off = pk[m2];
+        }
+        TRY(dalloc(h, &h->d_aptr, aptr.size()));
+        TRY(dalloc(h, &h->d_avi, avi.size()));
+        TRY(dalloc(h, &h->d_aw, aw.size()));
+        TRY(upload(h, aptr.data(), h->d_aptr, sizeof(int) * aptr.size()));
+        TRY(upload(h, avi.data(), h->d_avi, sizeof(int) * avi.size()));
+        TRY(upload(h, aw.data(), h->d_aw, sizeof(float) * aw.size()));
+        // mask tables of the full m x m grid (input of the adjoint's row pass)
+        std::vector<int> rs(m + 1), cl((size_t)m2), rc((size_t)m2);
+        for (int i = 0; i <= m; ++i) rs[i] = i * m;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) { cl[(size_t)i * m + j] = j; rc[(size_t)i * m + j] = (i << 16) | j; }
+        TRY(dalloc(h, &h->d_rowstart_m, m + 1));
+        TRY(dalloc(h, &h->d_col_m, m2));
+        TRY(dalloc(h, &h->d_rowcol_m, m2));
+        TRY(upload(h, rs.data(), h->d_rowstart_m, sizeof(int) * (m + 1)));
+        TRY(upload(h, cl.data(), h->d_col_m, sizeof(int) * m2));
+        TRY(upload(h, rc.data(), h->d_rowcol_m, sizeof(int) * m2));
+        h->mt_m = MaskTables{h->d_rowstart_m, h->d_col_m, h->d_rowcol_m, m2};
+        h->g_adj = MvmGeom{m, n, h->cos_layers, h->NP, h->Pc / 2 + 1, h->planc};
     }
 
     // --- workspaces --------------------------------------------------------------
@@ -806,6 +861,45 @@ void release(tomo_handle* h) {
     if (h->work) cudaStreamDestroy(h->work);
     if (h->h_nactive) cudaFreeHost(h->h_nactive);
     delete h;
+}
+
+// Conjugate-transposed projection spectra and workspaces of the adjoint, on
+// first use.
+tomo_status adjoint_init(tomo_handle* h) {
+    if (h->adj_ready) return TOMO_OK;
+    Launch L = launch_of(h);
+    const size_t nhc = h->Pc / 2 + 1;
+    const size_t kstride = (size_t)h->cos_layers * h->NP * nhc * h->Pc;
+    const size_t B = h->max_batch;
+    TRY(dalloc(h, &h->d_Kadj, kstride * h->n_targets));
+    for (int t = 0; t < h->n_targets; ++t)
+        CK(adjoint_spectra(L, (int)nhc, h->Pc, h->NP, h->cos_layers, h->d_Kc32 + t * kstride, h->d_Kadj + t * kstride));
+    TRY(dalloc(h, &h->Xa, B * h->cos_layers * nhc * h->m));
+    TRY(dalloc(h, &h->Ya, B * h->NP * nhc * h->n));
+    TRY(dalloc(h, &h->Yda, B * h->cos_layers * h->m * h->m));
+    TRY(dalloc(h, &h->za, B * h->N));
+    CK(cudaStreamSynchronize(h->stream));
+    h->adj_ready = true;
+    return TOMO_OK;
+}
+
+// zeta = sum_{t in [t0, t1)} W_s Sigma_s_phi_t W_phi^T phi[:, t] (the adjoint of
+// apply_os restricted to those targets), B <= max_batch frames.
+tomo_status apply_os_adjoint(tomo_handle* h, const Launch& L, const float* phi, float* zeta, int B, int t0, int t1) {
+    TRY(adjoint_init(h));
+    const size_t nhc = h->Pc / 2 + 1;
+    const size_t kstride = (size_t)h->cos_layers * h->NP * nhc * h->Pc;
+    for (int t = t0; t < t1; ++t) {
+        float* out = t == t0 ? zeta : h->za;
+        CK(interp_adjoint(L, B, h->n_targets, t, h->cos_layers, h->m, h->n_vphi, h->d_aptr, h->d_avi, h->d_aw, phi,
+                          h->Yda));
+        CK((rows_fwd<float, float>(L, h->g_adj, h->mt_m, B, h->Yda, nullptr, nullptr, h->Xa, h->d_twc32)));
+        CK((cols_mul<float>(L, h->g_adj, B, nullptr, h->Xa, h->Ya, h->d_Kadj + t * kstride, h->d_twc32, false)));
+        CK((rows_inv_masked<float, float>(L, h->g_adj, h->mt, B, nullptr, h->Ya, nullptr, h->d_noise_var, nullptr,
+                                          out, nullptr, h->d_twc32)));
+        if (t != t0) CK(axpy_f32(L, (size_t)B * h->N, 1.f, h->za, zeta));
+    }
+    return TOMO_OK;
 }
 
 // y = W_s F^{-1} M(f) F W_s^T x (the block-circulant preconditioner), FP32
@@ -1169,6 +1263,59 @@ tomo_status tomo_apply_cos(tomo_handle* h, const float* z, float* phi, int batch
         const int B = std::min(h->max_batch, batch - f0);
         TRY(apply_os(h, L, z + (size_t)f0 * h->N, phi + (size_t)f0 * h->n_targets * h->n_vphi, B));
     }
+    return TOMO_OK;
+}
+
+tomo_status tomo_apply_cos_adjoint(tomo_handle* h, const float* phi, float* z, int batch) {
+    if (!h || !phi || !z || batch < 0) return TOMO_EINVAL;
+    Launch L = launch_of(h);
+    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        TRY(apply_os_adjoint(h, L, phi + (size_t)f0 * h->n_targets * h->n_vphi, z + (size_t)f0 * h->N, B, 0,
+                             h->n_targets));
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_reconstructor(tomo_handle* h, int target, const tomo_solve_opts* opts, float* R,
+                               tomo_frame_info* info) {
+    if (!h || !R || target < 0 || target >= h->n_targets) return TOMO_EINVAL;
+    tomo_solve_opts o = opts ? *opts : default_opts();
+    TRY(check_opts(o));
+    if (o.warm_start) return TOMO_EINVAL;
+    if (h->modes) return TOMO_EINVAL;
+    Launch L = launch_of(h);
+    for (int v0 = 0; v0 < h->n_vphi; v0 += h->max_batch) {
+        const int B = std::min(h->max_batch, h->n_vphi - v0);
+        // right-hand sides W_s Sigma_s_phi W_phi^T e_v: columns of R^T's system
+        CK(unit_phase(L, B, h->n_targets, target, h->n_vphi, v0, h->phi_stage));
+        TRY(apply_os_adjoint(h, L, h->phi_stage, h->s_stage, B, target, target + 1));
+        TRY(solve_chunk(h, h->s_stage, B, o, R + (size_t)v0 * h->N, nullptr, info ? info + v0 : nullptr));
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_apply_reconstructor(tomo_handle* h, const float* R, int rows, const float* slopes, int batch,
+                                     float* phase) {
+    if (!h || !R || !slopes || !phase || rows < 1 || batch < 0) return TOMO_EINVAL;
+    if (batch == 0) return TOMO_OK;
+    Launch L = launch_of(h);
+    // enough K-splits that the grid covers the GPU several times, each split >= 256 columns
+    const long long tiles = (long long)((rows + 63) / 64) * ((batch + 63) / 64);
+    int splits = (int)std::min<long long>(32, std::max<long long>(1, (4LL * h->block_slots / 3 + tiles - 1) / tiles));
+    splits = std::max(1, std::min(splits, h->N / 256));
+    const size_t need = gemm_nt_workspace(batch, rows, splits);
+    if (need > h->gemm_part_size) {
+        if (h->gemm_part) {
+            CK(cudaStreamSynchronize(h->stream));
+            cudaFree(h->gemm_part);
+            h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)h->gemm_part), h->allocs.end());
+            h->gemm_part = nullptr;
+        }
+        TRY(dalloc(h, &h->gemm_part, need));
+        h->gemm_part_size = need;
+    }
+    CK(gemm_nt(L, batch, rows, h->N, slopes, h->N, R, h->N, phase, rows, splits, h->gemm_part));
     return TOMO_OK;
 }
 

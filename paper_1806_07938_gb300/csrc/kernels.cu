@@ -425,14 +425,18 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
             for (int r = 128 + lane; r < n; r += 32) dst[r] = src[r];
         }
     }
+    // an odd plane count leaves a pad plane in the last group: give it zeros
+    if (NPin & 1)
+        for (int i = threadIdx.x; i < nf * P; i += blockDim.x)
+            D[((size_t)(i / P) * NPmax + NPin) * P + i % P] = cmk<C>(0, 0);
     __syncthreads();
     {
-        const int gpf = NPin / G;                  // NPin is even
+        const int gpf = (NPin + G - 1) / G;        // the last group may include the pad plane
         for (int t = warp; t < nf * gpf; t += kWarps) {
             const int fl = t / gpf, q0 = (t % gpf) * G;
             if (!act[fl]) continue;
             C* base = D + ((size_t)fl * NPmax + q0) * P;
-            fft_g<PC, C, true>(base, P, G, g.plan, tw, scr + warp * P, lane, n, P);
+            fft_g<PC, C, true>(base, P, NPin - q0, g.plan, tw, scr + warp * P, lane, n, P);
         }
     }
     __syncthreads();
@@ -611,7 +615,7 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int rc = rowcol[e];
         const int row = rc >> 16, col = rc & 0xffff;
-        const TIn xi = __ldg(xin + vbase + e);
+        const TIn xi = xin ? __ldg(xin + vbase + e) : (TIn)0;
         const float ri = cgm ? __ldg(vr + vbase + e) : 0.f;
         const T v = reinterpret_cast<const T*>(F + ((row >> 1) - pb) * RS + col)[row & 1];
         const TIn out = cs * (TIn)v + nv * xi;

@@ -113,7 +113,7 @@ cudaError_t pack_hermitian(const Launch& L, int P, int NP, const float2* Kfull, 
 
 // Row-inverse pass to masked output (Sigma_ss): y = c_f crop/mask(IFFT rows) +
 // nu_f noise_var[plane] * xin, with (c_f, nu_f) = fscale[frame] ((1, 1) when
-// fscale is null).  CG mode (cg != nullptr; xin = cg->p, y = cg->Ap): also the
+// fscale is null); xin may be null (no diagonal term) outside CG mode.  CG mode (cg != nullptr; xin = cg->p, y = cg->Ap): also the
 // partial sums p^T Ap, r^T Ap, Ap^T Ap per (frame, plane).
 template <typename T, typename TIn>
 cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B,
@@ -168,6 +168,22 @@ cudaError_t count_active(const Launch& L, int B, const FrameState* st, int* n_ac
 template <typename TV>
 cudaError_t mode_project(const Launch& L, int B, int len, int nblk, int rg, const double* Q, const FrameState* st,
                          TV* y, const float* xin, const CgVecs* cg);
+
+// --- adjoint projection and explicit reconstructor (recon.cu) -----------------
+// out [B][n_layers][m][m] = I'^T of phi[:, t, :] through the transposed
+// bilinear table (ptr [n_layers][m*m + 1], vi / w entries: phase point, weight).
+cudaError_t interp_adjoint(const Launch& L, int B, int T_all, int t, int n_layers, int m, int n_vphi,
+                           const int* ptr, const int* vi, const float* w, const float* phi, float* out);
+// Kadj [nh][np][P][nq] = conj(K [nh][nq][P][np]).
+cudaError_t adjoint_spectra(const Launch& L, int nh, int P, int nq, int np, const float2* K, float2* Kadj);
+// phi [B][T][n_vphi]: unit vector at (t, v0 + f) for frame f.
+cudaError_t unit_phase(const Launch& L, int B, int T_all, int t, int n_vphi, int v0, float* phi);
+// C [M][N] (row stride ldc) = A [M][K] (lda) * B [N][K]^T (ldb), FP32, split
+// over K into `splits` partial tiles (part: gemm_nt_workspace floats) added
+// in a fixed order.
+size_t gemm_nt_workspace(int M, int N, int splits);
+cudaError_t gemm_nt(const Launch& L, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                    int ldc, int splits, float* part);
 
 // --- setup ------------------------------------------------------------------
 struct VkParams {

@@ -56,7 +56,8 @@ FRAME_INFO_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("s
 
 EXPORTS = ("tomo_create", "tomo_layout", "tomo_apply_css", "tomo_apply_css_noalloc", "tomo_apply_css_f64",
            "tomo_apply_cos",
-           "tomo_solve", "tomo_solve_r0", "tomo_solve_host", "tomo_autotune_result", "tomo_launch_count", "tomo_set_kernel_timing",
+           "tomo_solve", "tomo_solve_r0", "tomo_solve_host", "tomo_autotune_result",
+           "tomo_apply_cos_adjoint", "tomo_reconstructor", "tomo_apply_reconstructor", "tomo_launch_count", "tomo_set_kernel_timing",
            "tomo_apply_precond", "tomo_ws_init", "tomo_ws_param_count", "tomo_ws_set_params", "tomo_ws_get_params", "tomo_ws_apply",
            "tomo_ws_gradient", "tomo_ws_train_step",
            "tomo_get_kernel_timing", "tomo_destroy", "tomo_strerror")
@@ -91,6 +92,9 @@ def lib(path=None):
     L.tomo_solve.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_solve_host.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_autotune_result.argtypes = [vp, vp, vp, i, ctypes.POINTER(i)]
+    L.tomo_apply_cos_adjoint.argtypes = [vp, vp, vp, i]
+    L.tomo_reconstructor.argtypes = [vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp]
+    L.tomo_apply_reconstructor.argtypes = [vp, vp, i, vp, i, vp]
     L.tomo_solve_r0.argtypes = [vp, vp, i, vp, vp, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_launch_count.argtypes = [vp]
     L.tomo_launch_count.restype = ctypes.c_longlong
@@ -226,6 +230,27 @@ def tomo_solve(h, slopes, batch, opts, zeta, phase=None):
         h, _dptr(slopes, torch.float32), batch, ctypes.byref(opts), _dptr(zeta, torch.float32),
         _dptr(phase, torch.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)))
     return info
+
+
+def tomo_apply_cos_adjoint(h, phase, zeta, batch):
+    import torch
+    _check("tomo_apply_cos_adjoint", lib().tomo_apply_cos_adjoint(h, _dptr(phase, torch.float32),
+                                                                  _dptr(zeta, torch.float32), batch))
+
+
+def tomo_reconstructor(h, target, opts, R):
+    """Builds R [n_vphi][N] (device float32 tensor) of one target; returns the per-row info."""
+    import torch
+    info = np.zeros(R.shape[0], FRAME_INFO_DTYPE)
+    _check("tomo_reconstructor", lib().tomo_reconstructor(h, target, ctypes.byref(opts), _dptr(R, torch.float32),
+                                                          ctypes.c_void_p(info.ctypes.data)))
+    return info
+
+
+def tomo_apply_reconstructor(h, R, slopes, batch, phase):
+    import torch
+    _check("tomo_apply_reconstructor", lib().tomo_apply_reconstructor(
+        h, _dptr(R, torch.float32), R.shape[0], _dptr(slopes, torch.float32), batch, _dptr(phase, torch.float32)))
 
 
 def tomo_solve_r0(h, slopes, batch, r0, opts, zeta, phase=None, noise_scale=None):

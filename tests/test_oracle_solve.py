@@ -112,3 +112,14 @@ def test_minres_singular_consistent_system():
     b = A @ rng.standard_normal(10)
     x, _ = solve.minres(A, b, tol=1e-13, maxit=100)
     assert np.allclose(x, np.linalg.pinv(A) @ b, atol=1e-10)
+
+
+def test_reconstructor_definition(system):
+    # R A = F and R s = F A^{-1} s (the direct MVM reproduces the iterative estimate)
+    cfg, A, s = system
+    F = cov.cos_interp(cfg, 0)
+    R = solve.reconstructor(F, A)
+    assert R.shape == F.shape
+    assert np.abs(R @ A - F).max() <= 1e-9 * np.abs(F).max()
+    z = solve.solve_cholesky(A, s)
+    assert np.allclose(R @ s, F @ z, rtol=1e-9, atol=1e-9 * np.abs(F @ z).max())
