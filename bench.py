@@ -252,6 +252,68 @@ def train_warm_start(tomo, torch, h, cfg, layout, sub, seed, n_train=256, steps=
     return float(np.mean(losses[:5])), float(np.mean(losses[-20:]))
 
 
+def run_moao(tomo, torch, W, args, stream, flush, F, rank, world):
+    """MOAO variant: the elt_moao system (32 targets), F frames in four groups
+    generated at r0 = 0.10, 0.133, 0.167, 0.20 m and solved in one batch with
+    those per-frame r0 values (tomo_solve_r0), PCG to 1e-4, then the projection
+    to all 32 targets."""
+    import numpy as np
+    cfg = W.config("elt_moao")
+    r0s = [0.10, 0.133, 0.167, 0.20]
+    per = F // len(r0s)
+    parts, sigmas = [], []
+    for i, r0 in enumerate(r0s):
+        full, sigma = W.slope_frames_parallel(dict(cfg, r0=r0), per, seed=4000 + 10 * rank + i)
+        parts.append(full)
+        sigmas.append(sigma)
+    # the reconstructor's noise model: 3 % of the slope rms at the configuration's
+    # r0, scaled per frame to the noise its group was drawn with
+    _, sig = W.slope_frames(cfg, 1, seed=4000 + 10 * rank)
+    cfg["noise_sigma"] = [float(x) for x in sig]
+    nu = np.repeat([float(np.mean((sg / sig) ** 2)) for sg in sigmas], per)
+    t0 = time.perf_counter()
+    h = tomo.tomo_create(cfg, stream=stream, max_batch=F, precond=True)
+    create_s = time.perf_counter() - t0
+    try:
+        layout, sub, _ = tomo.tomo_layout(h)
+        B = per * len(r0s)
+        s = torch.tensor(tomo.valid_slopes(np.concatenate(parts), sub), dtype=torch.float32,
+                         device="cuda").contiguous()
+        r0v = np.repeat(np.array(r0s), per)
+        z = torch.zeros_like(s)
+        phi = torch.empty((B, layout.n_targets, layout.n_vphi), dtype=torch.float32, device="cuda")
+        opts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True)
+        for _ in range(args.warmup):
+            tomo.tomo_solve_r0(h, s, B, r0v, opts, z, phi, noise_scale=nu)
+        evs, info = [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = tomo.tomo_solve_r0(h, s, B, r0v, opts, z, phi, noise_scale=nu)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        # the projection alone (32 targets) on the solved zeta
+        pe0 = torch.cuda.Event(enable_timing=True)
+        pe1 = torch.cuda.Event(enable_timing=True)
+        pe0.record(stream)
+        tomo.tomo_apply_cos(h, z, phi, B)
+        pe1.record(stream)
+        torch.cuda.synchronize()
+        return {"value": world * B * args.steps / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / args.steps,
+                "frames": B, "targets": layout.n_targets, "r0": r0s, "noise_scale": sorted(set(nu.tolist())),
+                "iters_mean": float(info["iters"].mean()),
+                "iters_by_r0": [float(info["iters"][i * per:(i + 1) * per].mean()) for i in range(len(r0s))],
+                "all_converged": bool((info["status"] == 0).all() and (info["relres"] <= TOL).all()),
+                "projection_ms": pe0.elapsed_time(pe1), "create_s": create_s,
+                "workload": "elt_moao: the LGS part of config 4 (no NGS), 32 targets within 7', per-frame r0"}
+    finally:
+        tomo.tomo_destroy(h)
+
+
 def run_reference(args):
     world, rank, _, dist = dist_setup(False)
     if rank != 0:
@@ -348,7 +410,7 @@ def run_ours(args):
             return out
 
         # the same frames with the block-circulant preconditioner, and with MINRES (reported beside the headline)
-        pcg = minres = warm_prev = learned = single = direct = None
+        pcg = minres = warm_prev = learned = single = direct = moao = None
         if not args.no_variants:
             pcg = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True),
                           preconditioner=f"block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{{-1}} on the "
@@ -410,6 +472,9 @@ def run_ours(args):
                               "value excludes the build"}
             del R, phiR
             torch.cuda.empty_cache()
+            # batched MOAO, laser-star part: 32 target directions within 7', four
+            # seeings in one batch (per-frame r0), PCG, projection to every target
+            moao = run_moao(tomo, torch, W, args, stream, flush, F, rank, world)
             # closed-loop operation (Sec. 5): frozen-flow sequences at 1 kHz, each step
             # warm-started from the previous step's solution, PCG
             seq, _ = W.slope_sequence_parallel(cfg, F, args.warmup + args.steps + 1, seed=3000 + rank, dt=1e-3)
@@ -514,7 +579,7 @@ def run_ours(args):
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "pcg": pcg, "minres": minres, "learned_pcg": learned, "pcg_warm_previous": warm_prev,
-            "single_frame_pcg": single, "direct_mvm": direct,
+            "single_frame_pcg": single, "direct_mvm": direct, "moao_32_targets": moao,
             "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                       "relres_max": float(info["relres"].max()), "all_converged": ok,
                       "refinements_max": int(info["refinements"].max()),

@@ -17,6 +17,9 @@ Configurations (angles in radians, lengths in metres, r0 at 500 nm):
   a figure); r0 = 0.129 m, L0 = 25 m; noise 3 % of slope rms.
 * ``lgs_mid``  -- the ``elt_ltao`` system shrunk to 16 x 16 subapertures of the
   same size (8.43 m pupil), for tests the dense oracle finishes in seconds.
+* ``elt_moao`` -- the ``elt_ltao`` system with 32 target directions drawn
+  uniformly within a 7'-diameter field (seeded, seed 4): the laser-star part
+  of a batched MOAO system.
 
 Slope frames: per layer a periodic FFT phase screen with the von Karman PSD
 0.0228956 r0^{-5/3} (f^2 + 1/L0^2)^{-11/6} (Appendix A.1; the paper prints the
@@ -68,6 +71,13 @@ def config(name):
         return dict(name=name, D=39.0, obstruction=0.28, n=74, r0=0.129, L0=25.0,
                     layers=list(zip(NINE_LAYER_H, NINE_LAYER_FRAC)),
                     gs=ring(6, 30 * ARCSEC, 90e3), targets=[(0.0, 0.0)], noise_frac=0.03)
+    if name == "elt_moao":
+        cfg = config("elt_ltao")
+        rng = np.random.default_rng(4)
+        rad = 3.5 * 60 * ARCSEC * np.sqrt(rng.random(32))
+        ang = 2 * math.pi * rng.random(32)
+        cfg.update(name=name, targets=[(float(r * math.cos(a)), float(r * math.sin(a))) for r, a in zip(rad, ang)])
+        return cfg
     if name == "lgs_mid":
         return dict(name=name, D=16 * 39.0 / 74, obstruction=0.28, n=16, r0=0.129, L0=25.0,
                     layers=list(zip(NINE_LAYER_H, NINE_LAYER_FRAC)),
