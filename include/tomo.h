@@ -227,11 +227,20 @@ tomo_status tomo_apply_cos_adjoint(tomo_handle* h, const float* phase_dev, float
  * W_s Sigma_s_phi W_phi^T e_v (tomo_apply_cos_adjoint of a unit phase), so
  * R is built by n_vphi solves, max_batch at a time, with the options in opts
  * (NULL: tomo_solve's defaults; warm_start must be 0).  R_dev: device
- * [n_vphi][N] floats; info_host: NULL or [n_vphi] per-row solve outcomes.
- * TOMO_EINVAL with mode removal (cfg.mode_removal).  Uses the handle's
- * staging buffers of tomo_solve_host: do not run both at the same time. */
+ * [n_vphi][N] floats, or NULL to keep only the error below; info_host: NULL
+ * or [n_vphi] per-row solve outcomes.
+ * wfe_host: NULL or [3] doubles, the analytic wave-front error of this
+ * reconstructor for the target (Eq. analytical1, piston removed, mean over
+ * the valid phase points, rad^2 at the r0 wavelength): [0] the rms error
+ * sqrt([1] - [2]) [rad], [1] trace(P Sigma_phi_phi P) / n_vphi,
+ * [2] trace(P R Sigma_s_phi P) / n_vphi, taking the reconstructor's own
+ * covariance model as the truth (Hudgin slopes; for laser stars the
+ * interpolated Sigma_phi_s of Eq. ToeplitzLGS) and R = F A^{-1} as solved.
+ * R_dev and wfe_host cannot both be NULL.  TOMO_EINVAL with mode removal
+ * (cfg.mode_removal).  Uses the handle's staging buffers of tomo_solve_host:
+ * do not run both at the same time. */
 tomo_status tomo_reconstructor(tomo_handle* h, int target, const tomo_solve_opts* opts, float* R_dev,
-                               tomo_frame_info* info_host);
+                               tomo_frame_info* info_host, double* wfe_host);
 
 /* phase[b][v] = sum_j R[v][j] s[b][j]: the direct MVM with an explicit
  * reconstructor R_dev [rows][N] (e.g. from tomo_reconstructor), FP32,

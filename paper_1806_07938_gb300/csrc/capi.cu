@@ -69,6 +69,8 @@ struct tomo_handle {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     long long launches = 0;
     std::vector<uint8_t> subap_mask, phase_mask;
+    std::vector<int> ph_i, ph_j;       // valid phase points (row, column), row-major
+    double frac_sum = 1.0;             // sum of the Cn^2 fractions
     FftPlan plan{}, planc{};
     MvmGeom g_ss{}, g_os{};
     MaskTables mt{};
@@ -567,6 +569,10 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         for (int j = 0; j <= n; ++j)
             if (h->phase_mask[(size_t)i * (n + 1) + j]) { pv_i.push_back(i); pv_j.push_back(j); }
     h->n_vphi = (int)pv_i.size();
+    h->ph_i = pv_i;
+    h->ph_j = pv_j;
+    h->frac_sum = 0.0;
+    for (int k = 0; k < c->n_layers; ++k) h->frac_sum += c->layer_frac[k];
     if (c->mode_removal) {
         // Z_s: slopes of tip x, tilt y and focus x^2 + y^2 on one WFS; the
         // two-point slopes (Appendix A.2) of these modes at the subaperture
@@ -1278,21 +1284,80 @@ tomo_status tomo_apply_cos_adjoint(tomo_handle* h, const float* phi, float* z, i
 }
 
 tomo_status tomo_reconstructor(tomo_handle* h, int target, const tomo_solve_opts* opts, float* R,
-                               tomo_frame_info* info) {
-    if (!h || !R || target < 0 || target >= h->n_targets) return TOMO_EINVAL;
+                               tomo_frame_info* info, double* wfe) {
+    if (!h || (!R && !wfe) || target < 0 || target >= h->n_targets) return TOMO_EINVAL;
     tomo_solve_opts o = opts ? *opts : default_opts();
     TRY(check_opts(o));
     if (o.warm_start) return TOMO_EINVAL;
     if (h->modes) return TOMO_EINVAL;
     Launch L = launch_of(h);
-    for (int v0 = 0; v0 < h->n_vphi; v0 += h->max_batch) {
-        const int B = std::min(h->max_batch, h->n_vphi - v0);
-        // right-hand sides W_s Sigma_s_phi W_phi^T e_v: columns of R^T's system
-        CK(unit_phase(L, B, h->n_targets, target, h->n_vphi, v0, h->phi_stage));
-        TRY(apply_os_adjoint(h, L, h->phi_stage, h->s_stage, B, target, target + 1));
-        TRY(solve_chunk(h, h->s_stage, B, o, R + (size_t)v0 * h->N, nullptr, info ? info + v0 : nullptr));
+    const int nv = h->n_vphi;
+    double *dots = nullptr, *sums = nullptr;
+    if (wfe) {
+        TRY(dalloc(h, &dots, nv));
+        TRY(dalloc(h, &sums, 2 * (size_t)h->N));
+        CK(cudaMemsetAsync(sums, 0, sizeof(double) * 2 * h->N, h->stream));
     }
-    return TOMO_OK;
+    tomo_status st = TOMO_OK;
+    for (int v0 = 0; v0 < nv && st == TOMO_OK; v0 += h->max_batch) {
+        const int B = std::min(h->max_batch, nv - v0);
+        float* rows = R ? R + (size_t)v0 * h->N : h->z_stage;
+        // right-hand sides W_s Sigma_s_phi W_phi^T e_v: columns of R^T's system
+        CK(unit_phase(L, B, h->n_targets, target, nv, v0, h->phi_stage));
+        st = apply_os_adjoint(h, L, h->phi_stage, h->s_stage, B, target, target + 1);
+        if (st == TOMO_OK) st = solve_chunk(h, h->s_stage, B, o, rows, nullptr, info ? info + v0 : nullptr);
+        if (st == TOMO_OK && wfe) CK(wfe_accumulate(L, B, h->N, h->s_stage, rows, dots + v0, sums, sums + h->N));
+    }
+    if (st == TOMO_OK && wfe) {
+        // Eq. analytical1 for R = F A^{-1} (F = W_phi Sigma_phi_s W_s^T): the error
+        // covariance is Sigma_phi_phi - F A^{-1} F^T; piston removed (P = I - 1 1^T / n):
+        //   trace(P F A^{-1} F^T P) = sum_v F_v . R_v - (sum_v F_v) . (sum_v R_v) / n
+        //   trace(P S P) = n B(0) - sum_{u,v} B(|x_u - x_v|) / n
+        std::vector<double> hd(nv), hs(2 * (size_t)h->N);
+        CK(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(hs.data(), sums, sizeof(double) * 2 * h->N, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        double t2 = 0.0, cross = 0.0;
+        for (int v = 0; v < nv; ++v) t2 += hd[v];
+        for (int j = 0; j < h->N; ++j) cross += hs[j] * hs[(size_t)h->N + j];
+        t2 -= cross / nv;
+        // the target (at infinity) sees each layer through the pupil shifted by
+        // h_k beta, so Sigma_phi_phi depends only on x_u - x_v: one von Karman
+        // covariance with amplitude c_v (L0/r0)^{5/3} sum_k f_k, over the lags of
+        // the phase-point lattice weighted by how often each occurs
+        const int n = h->n, W = 2 * n + 1;
+        std::vector<long long> cnt((size_t)W * W, 0);
+        for (int u = 0; u < nv; ++u)
+            for (int v = 0; v < nv; ++v)
+                ++cnt[(size_t)(h->ph_i[u] - h->ph_i[v] + n) * W + (h->ph_j[u] - h->ph_j[v] + n)];
+        const double cv = std::pow(24.0 / 5.0 * std::tgamma(6.0 / 5.0), 5.0 / 6.0) * std::tgamma(11.0 / 6.0) *
+                          std::tgamma(5.0 / 6.0) / (2.0 * std::pow(kPi, 8.0 / 3.0));
+        const double B0 = cv * std::pow(h->L0 / h->r0, 5.0 / 3.0) * h->frac_sum;
+        const double norm = std::pow(2.0, 1.0 / 6.0) / std::tgamma(5.0 / 6.0);
+        double pair_sum = 0.0;
+        for (int di = -n; di <= n; ++di)
+            for (int dj = -n; dj <= n; ++dj) {
+                const long long c = cnt[(size_t)(di + n) * W + (dj + n)];
+                if (!c) continue;
+                const double rho = std::hypot((double)di, (double)dj) * h->d;
+                const double x = 2.0 * kPi * rho / h->L0;
+                const double b = rho == 0.0 ? B0 : B0 * norm * std::pow(x, 5.0 / 6.0) * std::cyl_bessel_k(5.0 / 6.0, x);
+                pair_sum += (double)c * b;
+            }
+        const double t1 = nv * B0 - pair_sum / nv;
+        wfe[1] = t1 / nv;
+        wfe[2] = t2 / nv;
+        wfe[0] = std::sqrt(std::max(0.0, (t1 - t2) / nv));
+    }
+    if (dots || sums) {
+        cudaStreamSynchronize(h->stream);
+        for (void* p : {(void*)dots, (void*)sums}) {
+            if (!p) continue;
+            cudaFree(p);
+            h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
+        }
+    }
+    return st;
 }
 
 tomo_status tomo_apply_reconstructor(tomo_handle* h, const float* R, int rows, const float* slopes, int batch,

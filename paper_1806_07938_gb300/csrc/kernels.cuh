@@ -181,6 +181,10 @@ cudaError_t unit_phase(const Launch& L, int B, int T_all, int t, int n_vphi, int
 // C [M][N] (row stride ldc) = A [M][K] (lda) * B [N][K]^T (ldb), FP32, split
 // over K into `splits` partial tiles (part: gemm_nt_workspace floats) added
 // in a fixed order.
+// dots[b] = F[b] . X[b]; sumF += sum_b F[b], sumX += sum_b X[b] (FP64, fixed
+// order): the terms of the analytic error of an explicit reconstructor.
+cudaError_t wfe_accumulate(const Launch& L, int B, int N, const float* F, const float* X, double* dots, double* sumF,
+                           double* sumX);
 size_t gemm_nt_workspace(int M, int N, int splits);
 cudaError_t gemm_nt(const Launch& L, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
                     int ldc, int splits, float* part);

@@ -127,7 +127,49 @@ __global__ void k_gemm_reduce(int M, int N, int splits, const float* __restrict_
     }
 }
 
+// sumF[j] += sum_b F[b][j], sumX[j] += sum_b X[b][j] (FP64, rows in order)
+__global__ void k_col_sums(int B, int N, const float* __restrict__ F, const float* __restrict__ X,
+                           double* __restrict__ sumF, double* __restrict__ sumX) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        double a = sumF[j], b = sumX[j];
+        for (int r = 0; r < B; ++r) {
+            a += (double)F[(size_t)r * N + j];
+            b += (double)X[(size_t)r * N + j];
+        }
+        sumF[j] = a;
+        sumX[j] = b;
+    }
+}
+
+// dots[b] = sum_j F[b][j] X[b][j] (FP64), one block per row
+__global__ void k_row_dots(int N, const float* __restrict__ F, const float* __restrict__ X, double* __restrict__ dots) {
+    __shared__ double red[8];
+    const int b = blockIdx.x;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) acc += (double)F[(size_t)b * N + j] * (double)X[(size_t)b * N + j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        dots[b] = t;
+    }
+}
+
 }  // namespace
+
+cudaError_t wfe_accumulate(const Launch& L, int B, int N, const float* F, const float* X, double* dots, double* sumF,
+                           double* sumX) {
+    if (B <= 0) return cudaSuccess;
+    k_row_dots<<<B, 256, 0, L.stream>>>(N, F, X, dots);
+    count(L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_col_sums<<<(N + 255) / 256, 256, 0, L.stream>>>(B, N, F, X, sumF, sumX);
+    count(L);
+    return cudaGetLastError();
+}
 
 cudaError_t interp_adjoint(const Launch& L, int B, int T_all, int t, int n_layers, int m, int n_vphi,
                            const int* ptr, const int* vi, const float* w, const float* phi, float* out) {

@@ -93,7 +93,7 @@ def lib(path=None):
     L.tomo_solve_host.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_autotune_result.argtypes = [vp, vp, vp, i, ctypes.POINTER(i)]
     L.tomo_apply_cos_adjoint.argtypes = [vp, vp, vp, i]
-    L.tomo_reconstructor.argtypes = [vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp]
+    L.tomo_reconstructor.argtypes = [vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_apply_reconstructor.argtypes = [vp, vp, i, vp, i, vp]
     L.tomo_solve_r0.argtypes = [vp, vp, i, vp, vp, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_launch_count.argtypes = [vp]
@@ -238,13 +238,18 @@ def tomo_apply_cos_adjoint(h, phase, zeta, batch):
                                                                   _dptr(zeta, torch.float32), batch))
 
 
-def tomo_reconstructor(h, target, opts, R):
-    """Builds R [n_vphi][N] (device float32 tensor) of one target; returns the per-row info."""
+def tomo_reconstructor(h, target, opts, R=None, n_rows=None, wfe=False):
+    """Builds R [n_vphi][N] (device float32 tensor, or None) of one target.
+    Returns the per-row info, and with wfe=True also the analytic error
+    (rms [rad], trace term of Sigma_phi_phi, trace term of R Sigma_s_phi)."""
     import torch
-    info = np.zeros(R.shape[0], FRAME_INFO_DTYPE)
-    _check("tomo_reconstructor", lib().tomo_reconstructor(h, target, ctypes.byref(opts), _dptr(R, torch.float32),
-                                                          ctypes.c_void_p(info.ctypes.data)))
-    return info
+    rows = R.shape[0] if R is not None else n_rows
+    info = np.zeros(rows, FRAME_INFO_DTYPE)
+    w = np.zeros(3, np.float64)
+    _check("tomo_reconstructor", lib().tomo_reconstructor(
+        h, target, ctypes.byref(opts), _dptr(R, torch.float32) if R is not None else None,
+        ctypes.c_void_p(info.ctypes.data), ctypes.c_void_p(w.ctypes.data) if wfe else None))
+    return (info, w) if wfe else info
 
 
 def tomo_apply_reconstructor(h, R, slopes, batch, phase):

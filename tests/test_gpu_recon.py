@@ -108,3 +108,22 @@ def test_apply_reconstructor_gemm(T, rows, batch, n, n_gs):
         assert relL2(out.double().cpu().numpy(), s @ R.T) <= 1e-5
     finally:
         T.tomo_destroy(h)
+
+
+@pytest.mark.parametrize("lgs", [False, True])
+def test_analytic_wfe_matches_oracle(T, lgs):
+    # Eq. analytical1 for the MMSE reconstructor, from the reconstructor build
+    from oracle import wfe
+    cfg = small_cfg(n=8, lgs=lgs, obstruction=0.2, D=4.0, noise=0.2, targets=((0.0, 0.0), (10e-6, 5e-6)))
+    ref = wfe.analytic_wfe(cfg, 1)
+    h = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=16)
+    try:
+        info, _, _ = T.tomo_layout(h)
+        rinfo, w = T.tomo_reconstructor(h, 1, T.solve_opts(tol=1e-6, max_iter=20000, max_refine=5), None,
+                                        n_rows=info.n_vphi, wfe=True)
+        print("wfe", w, "oracle", ref, "rms rad", np.sqrt(ref))
+        assert (rinfo["status"] == 0).all()
+        assert abs(w[0] ** 2 - ref) <= 1e-3 * ref
+        assert abs(w[0] ** 2 - (w[1] - w[2])) <= 1e-12 * w[1]
+    finally:
+        T.tomo_destroy(h)
