@@ -410,11 +410,14 @@ def run_ours(args):
             return out
 
         # the same frames with the block-circulant preconditioner, and with MINRES (reported beside the headline)
-        pcg = minres = warm_prev = learned = single = direct = moao = None
+        pcg = minres = warm_prev = learned = single = direct = moao = block = None
         if not args.no_variants:
             pcg = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True),
                           preconditioner=f"block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{{-1}} on the "
                                          f"{layout.P} x {layout.P} torus")
+            block = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, precond=True, method="block"),
+                            method="block PCG over the 64 frames (one Krylov space for the batch), block-circulant "
+                                   "preconditioner; iters = block iterations")
             minres = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=32, method="minres"),
                              method="MINRES in conjugate-residual form, unpreconditioned (as the paper ran it)")
             # single-frame latency: one frame per solve (the row passes then run
@@ -580,7 +583,7 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "pcg": pcg, "minres": minres, "learned_pcg": learned, "pcg_warm_previous": warm_prev,
+            "pcg": pcg, "block_pcg": block, "minres": minres, "learned_pcg": learned, "pcg_warm_previous": warm_prev,
             "single_frame_pcg": single, "direct_mvm": direct, "moao_32_targets": moao,
             "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                       "relres_max": float(info["relres"].max()), "all_converged": ok,

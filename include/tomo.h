@@ -121,7 +121,7 @@ typedef struct {
                               2: the initial guess is the warm-start network's  */
     int check_every;       /* iterations between host convergence checks (>= 1)   */
     int precond;           /* 1: preconditioned CG with the block-circulant M     */
-    int method;            /* TOMO_METHOD_CG (0) or TOMO_METHOD_MINRES (1)         */
+    int method;            /* TOMO_METHOD_CG (0), _MINRES (1) or _BLOCK (2)        */
 } tomo_solve_opts;
 
 /* Krylov method of tomo_solve (tomo_solve_opts.method).  The paper tests CG
@@ -130,8 +130,19 @@ typedef struct {
  * here each iterate minimises ||s - A zeta|| over the Krylov space, with one
  * operator product per iteration; it cannot be combined with precond = 1
  * (TOMO_EINVAL).  tomo_frame_info.iters counts operator products of the
- * iteration loop in both methods. */
-enum { TOMO_METHOD_CG = 0, TOMO_METHOD_MINRES = 1 };
+ * iteration loop in both methods.
+ * TOMO_METHOD_BLOCK: block conjugate gradients over the frames of each chunk
+ * of at most 64 frames (O'Leary; with precond = 1 the block-circulant
+ * preconditioner): every frame shares the operator, so one Krylov space,
+ * grown by the whole chunk at each iteration, serves all of them.  Each
+ * iteration applies the operator (and the preconditioner) to the chunk once,
+ * as the other methods do, plus FP64-accumulated Gram products of the block
+ * vectors and 64 x 64 FP64 algebra on the host; the search block is kept
+ * orthonormal by Cholesky QR with numerically dependent columns dropped.
+ * All frames of a chunk iterate until every one meets the tolerance; iters
+ * counts block iterations.  Needs max_batch <= 64 and one operator for all
+ * frames: tomo_solve_r0 rejects it (TOMO_EINVAL). */
+enum { TOMO_METHOD_CG = 0, TOMO_METHOD_MINRES = 1, TOMO_METHOD_BLOCK = 2 };
 
 typedef struct {
     int iters;             /* CG iterations summed over refinement passes         */

@@ -186,6 +186,15 @@ cudaError_t unit_phase(const Launch& L, int B, int T_all, int t, int n_vphi, int
 cudaError_t wfe_accumulate(const Launch& L, int B, int N, const float* F, const float* X, double* dots, double* sumF,
                            double* sumX);
 size_t gemm_nt_workspace(int M, int N, int splits);
+// Block recurrences over the frames of a batch (B <= 64 vectors [B][N]):
+// G [B][B] = U V^T (FP32 products, FP64 sums in a fixed order; part:
+// gram_workspace(N) doubles); Y = Y0 + C^T U, i.e. Y_j = Y0_j + sum_i C[i][j] U_i
+// (C [B][B] FP64, Y0 may be null, Y must not alias U); out [B][slices]: the
+// squared norm of each of `slices` column ranges of X_j (sum them for |X_j|^2).
+size_t gram_workspace(int N);
+cudaError_t gram(const Launch& L, int B, int N, const float* U, const float* V, double* G, double* part);
+cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const float* U, const float* Y0, float* Y);
+cudaError_t row_norms(const Launch& L, int B, int N, const float* X, double* out, int slices);
 cudaError_t gemm_nt(const Launch& L, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
                     int ldc, int splits, float* part);
 

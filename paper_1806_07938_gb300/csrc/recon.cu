@@ -15,6 +15,8 @@
 // phi[b][v] = sum_j R[v][j] s[b][j]: 64 x 64 output tiles, split over the
 // reduction dimension into a fixed number of partial tiles that a second
 // kernel adds in a fixed order (deterministic).
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace tomo {
@@ -208,6 +210,182 @@ cudaError_t gemm_nt(const Launch& L, int M, int N, int K, const float* A, int ld
     if (e != cudaSuccess) return e;
     k_gemm_reduce<<<1216, 256, 0, L.stream>>>(M, N, splits, part, C, ldc);
     count(L);
+    return cudaGetLastError();
+}
+
+}  // namespace tomo
+
+// ---------------------------------------------------------------------------
+// Block conjugate gradients over the frames of a batch (all frames share the
+// operator, so one Krylov space serves them all): the tall-skinny products
+// of the block recurrences.  Vectors are [B][N] (frame-major), B <= 64.
+// ---------------------------------------------------------------------------
+namespace tomo {
+
+namespace {
+
+constexpr int kBlockMax = 64;
+
+// Partial Gram tiles out[block][i][j] = sum over the block's columns of
+// U[i][k] V[j][k]: the block walks chunks of 64 columns (grid-strided), loads
+// each chunk of U and V with coalesced row reads into shared memory
+// (transposed), sums the chunk's 64 products in FP32 and adds them to FP64
+// accumulators, 4 x 4 outputs per thread.
+constexpr int kGramChunk = 64;
+
+__global__ void __launch_bounds__(256)
+k_gram_part(int B, int N, const float* __restrict__ U, const float* __restrict__ V, double* __restrict__ part) {
+    __shared__ __align__(16) float Us[kGramChunk][kBlockMax + 4];
+    __shared__ __align__(16) float Vs[kGramChunk][kBlockMax + 4];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    const int nchunks = (N + kGramChunk - 1) / kGramChunk;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int k0 = ch * kGramChunk;
+        for (int idx = threadIdx.x; idx < kBlockMax * kGramChunk; idx += blockDim.x) {
+            const int row = idx / kGramChunk, col = idx % kGramChunk, k = k0 + col;
+            const bool ok = row < B && k < N;
+            Us[col][row] = ok ? U[(size_t)row * N + k] : 0.f;
+            Vs[col][row] = ok ? V[(size_t)row * N + k] : 0.f;
+        }
+        __syncthreads();
+        float a32[4][4] = {};
+#pragma unroll 8
+        for (int kk = 0; kk < kGramChunk; ++kk) {
+            const float4 av = *reinterpret_cast<const float4*>(&Us[kk][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4*>(&Vs[kk][tx * 4]);
+            const float a[4] = {av.x, av.y, av.z, av.w};
+            const float b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a32[i][j] = fmaf(a[i], b[j], a32[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += (double)a32[i][j];
+        __syncthreads();
+    }
+    double* out = part + (size_t)blockIdx.x * kBlockMax * kBlockMax;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * kBlockMax + tx * 4 + j] = acc[i][j];
+}
+
+// G[i][j] = sum over the partial tiles: a block of 256 threads serves 32
+// entries; warp t sums tiles t, t + 8, t + 16, ... of its lane's entry
+// (coalesced across the warp), and the eight sums are added in a fixed order.
+__global__ void __launch_bounds__(256)
+k_gram_reduce(int B, int splits, const double* __restrict__ part, double* __restrict__ G) {
+    __shared__ double red[8][32];
+    const int t = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int e = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    for (int z = t; z < splits; z += 8) s += part[(size_t)z * kBlockMax * kBlockMax + e];
+    red[t][lane] = s;
+    __syncthreads();
+    if (t == 0) {
+        const double v = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                         ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+        const int i = e / kBlockMax, j = e % kBlockMax;
+        if (i < B && j < B) G[i * B + j] = v;
+    }
+}
+
+// Y[j][k] = (Y0 ? Y0[j][k] : 0) + sum_i C[i][j] U[i][k], one thread per column
+// k, four outputs at a time (independent sums).
+__global__ void __launch_bounds__(128)
+k_block_combine(int B, int N, const double* __restrict__ C, const float* __restrict__ U, const float* Y0,
+                float* Y) {
+    // C padded to 64 x 64 with zeros, so that the unrolled sums below add
+    // exact zeros for i >= B
+    __shared__ __align__(16) float Cs[kBlockMax * kBlockMax];   // read as float4
+    for (int t = threadIdx.x; t < kBlockMax * kBlockMax; t += blockDim.x) {
+        const int i = t / kBlockMax, j = t % kBlockMax;
+        Cs[t] = (i < B && j < B) ? (float)C[i * B + j] : 0.f;
+    }
+    __syncthreads();
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        float u[kBlockMax];
+#pragma unroll
+        for (int i = 0; i < kBlockMax; ++i) u[i] = i < B ? U[(size_t)i * N + k] : 0.f;
+        for (int j0 = 0; j0 < B; j0 += 4) {
+            float y[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) y[q] = (Y0 && j0 + q < B) ? Y0[(size_t)(j0 + q) * N + k] : 0.f;
+#pragma unroll
+            for (int i = 0; i < kBlockMax; ++i) {
+                const float4 c = *reinterpret_cast<const float4*>(&Cs[i * kBlockMax + j0]);
+                y[0] = fmaf(c.x, u[i], y[0]);
+                y[1] = fmaf(c.y, u[i], y[1]);
+                y[2] = fmaf(c.z, u[i], y[2]);
+                y[3] = fmaf(c.w, u[i], y[3]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j0 + q < B) Y[(size_t)(j0 + q) * N + k] = y[q];
+        }
+    }
+}
+
+// out[j][s] = sum over the s-th of S column slices of X[j][k]^2 (FP64)
+__global__ void k_row_norms(int N, int S, const float* __restrict__ X, double* __restrict__ out) {
+    __shared__ double red[8];
+    const int b = blockIdx.x, sl = blockIdx.y;
+    const int k0 = (int)((long long)N * sl / S), k1 = (int)((long long)N * (sl + 1) / S);
+    double acc = 0.0;
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const double v = X[(size_t)b * N + k];
+        acc += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        out[(size_t)b * S + sl] = t;
+    }
+}
+
+inline void count2(const Launch& L) {
+    if (L.counter) ++*L.counter;
+}
+
+}  // namespace
+
+constexpr int kGramBlocks = 2 * 152;
+
+size_t gram_workspace(int /*N*/) { return (size_t)kGramBlocks * kBlockMax * kBlockMax; }
+
+cudaError_t gram(const Launch& L, int B, int N, const float* U, const float* V, double* G, double* part) {
+    if (B < 1 || B > kBlockMax || N < 1) return cudaErrorInvalidValue;
+    const int nchunks = (N + kGramChunk - 1) / kGramChunk;
+    const int blocks = std::min(kGramBlocks, nchunks);
+    k_gram_part<<<blocks, 256, 0, L.stream>>>(B, N, U, V, part);
+    count2(L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gram_reduce<<<kBlockMax * kBlockMax / 32, 256, 0, L.stream>>>(B, blocks, part, G);
+    count2(L);
+    return cudaGetLastError();
+}
+
+cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const float* U, const float* Y0, float* Y) {
+    if (B < 1 || B > kBlockMax) return cudaErrorInvalidValue;
+    const int blocks = (N + 127) / 128;
+    k_block_combine<<<blocks, 128, 0, L.stream>>>(B, N, C, U, Y0, Y);
+    count2(L);
+    return cudaGetLastError();
+}
+
+cudaError_t row_norms(const Launch& L, int B, int N, const float* X, double* out, int slices) {
+    if (B <= 0) return cudaSuccess;
+    if (slices < 1) return cudaErrorInvalidValue;
+    k_row_norms<<<dim3(B, slices), 256, 0, L.stream>>>(N, slices, X, out);
+    count2(L);
     return cudaGetLastError();
 }
 

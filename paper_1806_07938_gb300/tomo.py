@@ -212,12 +212,12 @@ def tomo_apply_cos(h, zeta, phase, batch):
     _check("tomo_apply_cos", lib().tomo_apply_cos(h, _dptr(zeta, torch.float32), _dptr(phase, torch.float32), batch))
 
 
-METHODS = {"cg": 0, "minres": 1}
+METHODS = {"cg": 0, "minres": 1, "block": 2}
 
 
 def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=0, check_every=32, precond=False, method="cg"):
     """warm_start: 0 cold, 1 zeta holds the guess, 2 the warm-start network's guess;
-    method: "cg" or "minres"."""
+    method: "cg", "minres" or "block" (block CG over the frames of a chunk)."""
     return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every, int(bool(precond)),
                            METHODS[method])
 
