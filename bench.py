@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="time only the headline plain-CG solve (no PCG, MINRES, closed-loop or learned variants)")
+    ap.add_argument("--fft-P", type=int, default=-1,
+                    help="FFT side of the Sigma_ss product (-1: autotuned; profiling runs pin it, since the "
+                         "autotuner's timings are distorted under a profiler)")
+    ap.add_argument("--profile-block", action="store_true",
+                    help="for profiling: solve the frames W + K times with block PCG and nothing else, print a "
+                         "short JSON line (not a bench result)")
     return ap.parse_args()
 
 
@@ -352,13 +358,22 @@ def run_ours(args):
     F = args.frames
     with torch.cuda.stream(stream):
         # fft_P = -1: the library times the candidate FFT sides and keeps the fastest
-        h = tomo.tomo_create(cfg, stream=stream, max_batch=F, precond=True, fft_P=-1)
+        h = tomo.tomo_create(cfg, stream=stream, max_batch=F, precond=True, fft_P=args.fft_P)
         layout, sub, ph = tomo.tomo_layout(h)
         tune_P, tune_ms = tomo.tomo_autotune_result(h)
         s = torch.tensor(tomo.valid_slopes(full, sub), dtype=torch.float32, device="cuda").contiguous()
         z = torch.zeros_like(s)
         phi = torch.empty((F, layout.n_targets, layout.n_vphi), dtype=torch.float32, device="cuda")
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        if args.profile_block:
+            bopts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, precond=True, method="block")
+            for _ in range(args.warmup + args.steps):
+                binfo = tomo.tomo_solve(h, s, F, bopts, z, phi)
+            torch.cuda.synchronize()
+            print(json.dumps({"profile": "block_pcg", "iters": int(binfo["iters"][0]),
+                              "relres_max": float(binfo["relres"].max())}), flush=True)
+            tomo.tomo_destroy(h)
+            return
         opts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=32)
         for _ in range(args.warmup):
             tomo.tomo_solve(h, s, F, opts, z, phi)
