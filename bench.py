@@ -425,7 +425,7 @@ def run_ours(args):
             return out
 
         # the same frames with the block-circulant preconditioner, and with MINRES (reported beside the headline)
-        pcg = minres = warm_prev = learned = single = direct = moao = block = None
+        pcg = minres = warm_prev = learned = single = direct = moao = block = learned_block = None
         if not args.no_variants:
             pcg = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=True),
                           preconditioner=f"block-circulant: per-frequency (K_+(f) + 3 sigma^2)^{{-1}} on the "
@@ -533,6 +533,9 @@ def run_ours(args):
                                                   warm_start=2),
                                   training={"frames": 256, "steps": 200, "loss_first": l0, "loss_last": l1,
                                             "network": "3x3 CNN 12-32-32-32-12, FP32, warm start of the PCG"})
+                learned_block = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, precond=True,
+                                                        warm_start=2, method="block"),
+                                        note="the same network as warm start of block PCG")
         total_ms = sum(step_ms)
         if dist:
             t = torch.tensor([total_ms], device="cuda")
@@ -598,7 +601,8 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "pcg": pcg, "block_pcg": block, "minres": minres, "learned_pcg": learned, "pcg_warm_previous": warm_prev,
+            "pcg": pcg, "block_pcg": block, "minres": minres, "learned_pcg": learned,
+            "learned_block_pcg": learned_block, "pcg_warm_previous": warm_prev,
             "single_frame_pcg": single, "direct_mvm": direct, "moao_32_targets": moao,
             "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                       "relres_max": float(info["relres"].max()), "all_converged": ok,
