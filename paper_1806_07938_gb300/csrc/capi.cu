@@ -1132,26 +1132,26 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         // well conditioned: folding the QR factor into the coefficients
         // instead measured 142 against 112 block iterations at ELT scale.
         if (!h->d_small) {
-            TRY(dalloc(h, &h->d_small, 8 * 64 * 64));
+            TRY(dalloc(h, &h->d_small, 9 * 64 * 64));
             TRY(dalloc(h, &h->d_gram_part, gram_workspace(h->N)));
-            CK(cudaMallocHost(&h->h_small, sizeof(double) * 8 * 64 * 64));
+            CK(cudaMallocHost(&h->h_small, sizeof(double) * 9 * 64 * 64));
         }
         // small FP64 matrices, device and pinned host at the same offsets:
-        // [G | H] [E | norms] [alpha | -alpha] [beta] [T] [Gw]
+        // [G] [norms] [H] [E] [T_G] [T_W] [Gw] [alpha / beta] [work]
         constexpr size_t kS = 4096;
         constexpr int kNormSlices = 16;
         double* dG = h->d_small;
-        double* dH = dG + kS;
-        double* dE = dG + 2 * kS;
-        double* dRR = dG + 3 * kS;
-        double* dA = dG + 4 * kS;
-        double* dA2 = dG + 5 * kS;
-        double* dBt = dG + 6 * kS;
-        double* dT = dG + 7 * kS;
-        double* dGw = dBt;                               // Gw shares beta's slot (never live together)
+        double* dRR = dG + kS;                           // [B][16] partial norms, right after G
+        double* dH = dG + 2 * kS;
+        double* dE = dG + 3 * kS;
+        double* dTG = dG + 4 * kS;
+        double* dTW = dG + 5 * kS;
+        double* dGw = dG + 6 * kS;
+        double* dAB = dG + 7 * kS;                       // alpha, then beta
+        double* dWk = dG + 8 * kS;                       // T_G^T H (a product never writes its inputs)
         double* hs = h->h_small;
         const size_t BB = (size_t)B * B;
-        std::vector<double> G(BB), H(BB), E(BB), Gw(BB), C, LG, LW, tol2(B);
+        std::vector<double> G(BB), Gw(BB), C, LG, LW, tol2(B);
         std::vector<char> dropG, dropW;
         auto d2h = [&](const double* d, size_t n) -> tomo_status {
             CK(cudaMemcpyAsync(hs + (d - h->d_small), d, sizeof(double) * n, cudaMemcpyDeviceToHost, h->work));
@@ -1172,17 +1172,14 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, out, nullptr, nullptr));
             return TOMO_OK;
         };
-        // W -> P with orthonormal columns (Cholesky QR)
-        auto orth = [&](const float* W) -> tomo_status {
-            CK(gram(L, B, h->N, W, W, dGw, h->d_gram_part));
-            TRY(d2h(dGw, BB));
-            CK(cudaStreamSynchronize(h->work));
-            std::copy(hv(dGw), hv(dGw) + BB, Gw.begin());
-            chol_drop(Gw, B, 1e-6, LW, dropW);
-            chol_inv_t(LW, dropW, B, C);
+        // T = L^{-T} of the Cholesky factor of the Gram matrix at d (host), to dT
+        auto factor = [&](const double* dGram, std::vector<double>& Gh, double rel_drop, std::vector<double>& Lf,
+                          std::vector<char>& drop, double* dT) -> tomo_status {
+            std::copy(hv(dGram), hv(dGram) + BB, Gh.begin());
+            chol_drop(Gh, B, rel_drop, Lf, drop);
+            chol_inv_t(Lf, drop, B, C);
             std::copy(C.begin(), C.end(), hv(dT));
             TRY(h2d(dT, BB));
-            CK(block_combine(L, B, h->N, dT, W, nullptr, h->p));
             return TOMO_OK;
         };
         {
@@ -1194,49 +1191,56 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         block_iters = 0;
         bool done = false;
         while (!done) {
-            // (re)start from the residual in r
-            const float* Z = h->r;
-            if (pcg) { TRY(apply_M(h->r, h->z)); Z = h->z; }
-            TRY(orth(Z));
+            // (re)start from the residual in r: W = M r (or r), P = W T_W
+            const float* W = h->r;
+            if (pcg) { TRY(apply_M(h->r, h->z)); W = h->z; }
+            CK(gram(L, B, h->N, W, W, dGw, h->d_gram_part));
+            TRY(d2h(dGw, BB));
+            CK(cudaStreamSynchronize(h->work));
+            TRY(factor(dGw, Gw, 1e-6, LW, dropW, dTW));
             bool converged = false;
+            bool have_norms = false;
             while (!converged) {
                 if (block_iters >= (long long)o.max_iter) break;
+                // P = W T_W (orthonormal columns), A P, and the Gram products with P
+                CK(block_combine(L, B, h->N, dTW, W, nullptr, h->p));
                 TRY(apply_A(h->p, h->Ap));
                 CK(gram(L, B, h->N, h->p, h->Ap, dG, h->d_gram_part));
                 CK(gram(L, B, h->N, h->p, h->r, dH, h->d_gram_part));
-                TRY(d2h(dG, kS + BB));                         // G and H
+                // G and the residual norms of the previous update in one copy
+                TRY(d2h(dG, kS + (size_t)B * kNormSlices));
                 CK(cudaStreamSynchronize(h->work));
-                std::copy(hv(dG), hv(dG) + BB, G.begin());
-                std::copy(hv(dH), hv(dH) + BB, H.begin());
-                chol_drop(G, B, 1e-13, LG, dropG);
-                chol_solve(LG, dropG, B, H, 1.0, C);           // alpha
-                double* ha = hv(dA);
-                double* ha2 = hv(dA2);
-                for (size_t i = 0; i < BB; ++i) { ha[i] = C[i]; ha2[i] = -C[i]; }
-                TRY(h2d(dA, kS + BB));                         // alpha and -alpha
-                CK(block_combine(L, B, h->N, dA, h->p, h->x, h->x));
-                CK(block_combine(L, B, h->N, dA2, h->Ap, h->r, h->r));
+                if (have_norms) {
+                    const double* rrs = hv(dRR);
+                    converged = true;
+                    for (int f = 0; f < B; ++f) {
+                        double t = 0.0;
+                        for (int q = 0; q < kNormSlices; ++q) t += rrs[(size_t)f * kNormSlices + q];
+                        converged = converged && t <= tol2[f];
+                    }
+                    if (converged) break;
+                }
+                TRY(factor(dG, G, 1e-13, LG, dropG, dTG));
+                // alpha = G^+ P^T r = T_G T_G^T H on the device; x += P alpha, r -= A P alpha
+                CK(small_gemm(L, B, dTG, dH, dWk, true, 1.0));
+                CK(small_gemm(L, B, dTG, dWk, dAB, false, 1.0));
+                CK(block_combine(L, B, h->N, dAB, h->p, h->x, h->x));
+                CK(block_combine(L, B, h->N, dAB, h->Ap, h->r, h->r, -1.0));
                 ++block_iters;
                 CK(row_norms(L, B, h->N, h->r, dRR, kNormSlices));
-                Z = h->r;
+                have_norms = true;
+                const float* Z = h->r;
                 if (pcg) { TRY(apply_M(h->r, h->z)); Z = h->z; }
+                // beta = -G^+ (A P)^T z; next W = z + P beta
                 CK(gram(L, B, h->N, h->Ap, Z, dE, h->d_gram_part));
-                TRY(d2h(dE, kS + (size_t)B * kNormSlices));    // E and the residual norms
+                CK(small_gemm(L, B, dTG, dE, dWk, true, 1.0));
+                CK(small_gemm(L, B, dTG, dWk, dAB, false, -1.0));
+                CK(block_combine(L, B, h->N, dAB, h->p, Z, h->w));
+                W = h->w;
+                CK(gram(L, B, h->N, W, W, dGw, h->d_gram_part));
+                TRY(d2h(dGw, BB));
                 CK(cudaStreamSynchronize(h->work));
-                std::copy(hv(dE), hv(dE) + BB, E.begin());
-                const double* rrs = hv(dRR);
-                converged = true;
-                for (int f = 0; f < B; ++f) {
-                    double t = 0.0;
-                    for (int q = 0; q < kNormSlices; ++q) t += rrs[(size_t)f * kNormSlices + q];
-                    converged = converged && t <= tol2[f];
-                }
-                if (converged) break;
-                chol_solve(LG, dropG, B, E, -1.0, C);          // beta
-                std::copy(C.begin(), C.end(), hv(dBt));
-                TRY(h2d(dBt, BB));
-                CK(block_combine(L, B, h->N, dBt, h->p, Z, h->w));
-                TRY(orth(h->w));
+                TRY(factor(dGw, Gw, 1e-6, LW, dropW, dTW));
             }
             if (!converged) {
                 // iteration budget spent

@@ -193,7 +193,10 @@ size_t gemm_nt_workspace(int M, int N, int splits);
 // squared norm of each of `slices` column ranges of X_j (sum them for |X_j|^2).
 size_t gram_workspace(int N);
 cudaError_t gram(const Launch& L, int B, int N, const float* U, const float* V, double* G, double* part);
-cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const float* U, const float* Y0, float* Y);
+cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const float* U, const float* Y0, float* Y,
+                          double scale = 1.0);
+// Y = scale op(A) X for B x B FP64 matrices, op(A) = A or A^T (Y must not alias A or X).
+cudaError_t small_gemm(const Launch& L, int B, const double* A, const double* X, double* Y, bool transA, double scale);
 cudaError_t row_norms(const Launch& L, int B, int N, const float* X, double* out, int slices);
 cudaError_t gemm_nt(const Launch& L, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
                     int ldc, int splits, float* part);

@@ -297,14 +297,14 @@ k_gram_reduce(int B, int splits, const double* __restrict__ part, double* __rest
 // Y[j][k] = (Y0 ? Y0[j][k] : 0) + sum_i C[i][j] U[i][k], one thread per column
 // k, four outputs at a time (independent sums).
 __global__ void __launch_bounds__(128)
-k_block_combine(int B, int N, const double* __restrict__ C, const float* __restrict__ U, const float* Y0,
-                float* Y) {
+k_block_combine(int B, int N, const double* __restrict__ C, double scale, const float* __restrict__ U,
+                const float* Y0, float* Y) {
     // C padded to 64 x 64 with zeros, so that the unrolled sums below add
     // exact zeros for i >= B
     __shared__ __align__(16) float Cs[kBlockMax * kBlockMax];   // read as float4
     for (int t = threadIdx.x; t < kBlockMax * kBlockMax; t += blockDim.x) {
         const int i = t / kBlockMax, j = t % kBlockMax;
-        Cs[t] = (i < B && j < B) ? (float)C[i * B + j] : 0.f;
+        Cs[t] = (i < B && j < B) ? (float)(scale * C[i * B + j]) : 0.f;
     }
     __syncthreads();
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
@@ -328,6 +328,17 @@ k_block_combine(int B, int N, const double* __restrict__ C, const float* __restr
                 if (j0 + q < B) Y[(size_t)(j0 + q) * N + k] = y[q];
         }
     }
+}
+
+// Y = scale * op(A) X for B x B FP64 matrices (row-major), op(A) = A or A^T:
+// one block per row of Y, one thread per column.
+__global__ void k_small_gemm(int B, const double* __restrict__ A, const double* __restrict__ X, double* __restrict__ Y,
+                             int transA, double scale) {
+    const int i = blockIdx.x, j = threadIdx.x;
+    if (i >= B || j >= B) return;
+    double acc = 0.0;
+    for (int k = 0; k < B; ++k) acc += (transA ? A[k * B + i] : A[i * B + k]) * X[k * B + j];
+    Y[i * B + j] = scale * acc;
 }
 
 // out[j][s] = sum over the s-th of S column slices of X[j][k]^2 (FP64)
@@ -373,10 +384,18 @@ cudaError_t gram(const Launch& L, int B, int N, const float* U, const float* V, 
     return cudaGetLastError();
 }
 
-cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const float* U, const float* Y0, float* Y) {
+cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const float* U, const float* Y0, float* Y,
+                          double scale) {
     if (B < 1 || B > kBlockMax) return cudaErrorInvalidValue;
     const int blocks = (N + 127) / 128;
-    k_block_combine<<<blocks, 128, 0, L.stream>>>(B, N, C, U, Y0, Y);
+    k_block_combine<<<blocks, 128, 0, L.stream>>>(B, N, C, scale, U, Y0, Y);
+    count2(L);
+    return cudaGetLastError();
+}
+
+cudaError_t small_gemm(const Launch& L, int B, const double* A, const double* X, double* Y, bool transA, double scale) {
+    if (B < 1 || B > kBlockMax) return cudaErrorInvalidValue;
+    k_small_gemm<<<B, kBlockMax, 0, L.stream>>>(B, A, X, Y, transA ? 1 : 0, scale);
     count2(L);
     return cudaGetLastError();
 }
