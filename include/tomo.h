@@ -141,7 +141,7 @@ typedef struct {
  * orthonormal by Cholesky QR with numerically dependent columns dropped.
  * All frames of a chunk iterate until every one meets the tolerance; iters
  * counts block iterations.  Needs max_batch <= 64 and one operator for all
- * frames: tomo_solve_r0 rejects it (TOMO_EINVAL). */
+ * frames up to a factor per frame (see tomo_solve_r0). */
 enum { TOMO_METHOD_CG = 0, TOMO_METHOD_MINRES = 1, TOMO_METHOD_BLOCK = 2 };
 
 typedef struct {
@@ -286,7 +286,13 @@ tomo_status tomo_solve(tomo_handle* h, const float* slopes_dev, int batch,
  * NULL; both host memory, read before the call returns.  The preconditioner,
  * if used, is the configuration's one scaled by 1 / c_f (exact when
  * nu_f = c_f).  Other arguments and results as tomo_solve; TOMO_EINVAL for a
- * non-positive or non-finite r0 or a negative noise scale. */
+ * non-positive or non-finite r0 or a negative noise scale.
+ * With TOMO_METHOD_BLOCK the operators of all frames must be multiples of one
+ * another, i.e. kappa = nu_f / c_f the same for every frame (as when the noise
+ * variance follows the seeing); the library then solves the common system
+ * (Sigma_ss + kappa Sigma_eta_eta) zeta~_f = s_f by block CG and returns
+ * zeta_f = zeta~_f / c_f (and phi_f = c_f Cos zeta_f = Cos zeta~_f).  Other
+ * mixes are TOMO_EINVAL. */
 tomo_status tomo_solve_r0(tomo_handle* h, const float* slopes_dev, int batch,
                           const double* r0_host, const double* noise_scale_host,
                           const tomo_solve_opts* opts, float* zeta_dev, float* phase_dev,

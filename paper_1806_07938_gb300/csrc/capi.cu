@@ -114,6 +114,8 @@ struct tomo_handle {
     // block CG: small FP64 matrices [5][64 x 64] and the Gram workspace
     double* d_small = nullptr;
     double* h_small = nullptr;         // pinned host mirror of d_small
+    // block solves of proportional per-frame operators (tomo_solve_r0): 1 / c_f
+    double* d_rhs_scale = nullptr;
     double* d_gram_part = nullptr;
     // FFT-side autotuning (cfg.fft_P < 0): candidate sides and their measured
     // Sigma_ss product times [ms] (negative: the side could not run)
@@ -1069,7 +1071,8 @@ tomo_status set_fscale(tomo_handle* h, int B, const double* c, const double* nu)
 }
 
 tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_opts& o, float* zeta, float* phase,
-                        tomo_frame_info* info, const double* c_scale = nullptr, const double* nu_scale = nullptr) {
+                        tomo_frame_info* info, const double* c_scale = nullptr, const double* nu_scale = nullptr,
+                        const double* prop_c = nullptr) {
     // the solve runs on the private stream, ordered after the caller's stream
     // and before anything the caller enqueues next
     Launch L{h->work, &h->launches};
@@ -1077,6 +1080,16 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
     CK(cudaEventRecord(h->ev_in, h->stream));
     CK(cudaStreamWaitEvent(h->work, h->ev_in, 0));
     const int ms_len = 2 * h->n_vs;
+    if (prop_c) {
+        // proportional operators A_f = c_f A~ (the caller passes the common
+        // A~ as c = 1, nu = kappa): solve A~ zeta~_f = s_f (same relative
+        // residual), then zeta_f = zeta~_f / c_f and phi_f = c_f Cos zeta_f = Cos zeta~_f
+        if (!h->d_rhs_scale) TRY(dalloc(h, &h->d_rhs_scale, h->max_batch));
+        std::vector<double> inv(B);
+        for (int f = 0; f < B; ++f) inv[f] = 1.0 / prop_c[f];
+        CK(cudaMemcpyAsync(h->d_rhs_scale, inv.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->work));
+        CK(cudaStreamSynchronize(h->work));
+    }
     if (h->modes) {
         // right-hand side M_s s
         CK(cudaMemcpyAsync(h->s_proj, s, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
@@ -1309,7 +1322,8 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         total_iters += chunk;
     }
     if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->x, nullptr, nullptr));
-    CK(cudaMemcpyAsync(zeta, h->x, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
+    if (prop_c) CK(scale_rows(L, B, h->N, h->d_rhs_scale, h->x, zeta));
+    else CK(cudaMemcpyAsync(zeta, h->x, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
     if (phase) {
         TRY(apply_os(h, L, h->x, phase, B, h->d_fscale));
         if (h->modes)
@@ -1634,13 +1648,29 @@ tomo_status tomo_solve_r0(tomo_handle* h, const float* slopes, int batch, const 
     if (!h || !slopes || !zeta || !r0 || batch < 0) return TOMO_EINVAL;
     tomo_solve_opts o = opts ? *opts : default_opts();
     TRY(check_opts(o, h->max_batch));
-    if (o.method == TOMO_METHOD_BLOCK) return TOMO_EINVAL;     // one Krylov space needs one operator
     // von Karman covariances scale as r0^{-5/3} (B(0) = c_v (L0 / r0)^{5/3})
     std::vector<double> c(batch);
     for (int f = 0; f < batch; ++f) {
         if (!(r0[f] > 0) || !std::isfinite(r0[f])) return TOMO_EINVAL;
         if (noise_scale && !(noise_scale[f] >= 0 && std::isfinite(noise_scale[f]))) return TOMO_EINVAL;
         c[f] = std::pow(r0[f] / h->r0, -5.0 / 3.0);
+    }
+    if (o.method == TOMO_METHOD_BLOCK) {
+        // one Krylov space needs one operator up to a factor per frame:
+        // A_f = c_f (Sigma_ss + kappa Sigma_eta_eta) with kappa = nu_f / c_f common
+        const double kappa = (noise_scale ? noise_scale[0] : 1.0) / c[0];
+        for (int f = 0; f < batch; ++f) {
+            const double kf = (noise_scale ? noise_scale[f] : 1.0) / c[f];
+            if (!(std::fabs(kf - kappa) <= 1e-9 * std::max(kappa, 1e-300))) return TOMO_EINVAL;
+        }
+        std::vector<double> one((size_t)h->max_batch, 1.0), kap((size_t)h->max_batch, kappa);
+        for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+            const int B = std::min(h->max_batch, batch - f0);
+            TRY(solve_chunk(h, slopes + (size_t)f0 * h->N, B, o, zeta + (size_t)f0 * h->N,
+                            phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr, info ? info + f0 : nullptr,
+                            one.data(), kap.data(), c.data() + f0));
+        }
+        return TOMO_OK;
     }
     for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
         const int B = std::min(h->max_batch, batch - f0);

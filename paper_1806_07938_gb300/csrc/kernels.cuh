@@ -198,6 +198,8 @@ cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const 
 // Y = scale op(A) X for B x B FP64 matrices, op(A) = A or A^T (Y must not alias A or X).
 cudaError_t small_gemm(const Launch& L, int B, const double* A, const double* X, double* Y, bool transA, double scale);
 cudaError_t row_norms(const Launch& L, int B, int N, const float* X, double* out, int slices);
+// Y_j = f[j] X_j (device FP64 factors; Y may alias X).
+cudaError_t scale_rows(const Launch& L, int B, int N, const double* f, const float* X, float* Y);
 cudaError_t gemm_nt(const Launch& L, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
                     int ldc, int splits, float* part);
 

@@ -341,6 +341,14 @@ __global__ void k_small_gemm(int B, const double* __restrict__ A, const double* 
     Y[i * B + j] = scale * acc;
 }
 
+// Y[j][k] = f[j] X[j][k] (per-row scale; Y may alias X)
+__global__ void k_scale_rows(int B, int N, const double* __restrict__ f, const float* X, float* Y) {
+    const int j = blockIdx.y;
+    const float a = (float)f[j];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x)
+        Y[(size_t)j * N + k] = a * X[(size_t)j * N + k];
+}
+
 // out[j][s] = sum over the s-th of S column slices of X[j][k]^2 (FP64)
 __global__ void k_row_norms(int N, int S, const float* __restrict__ X, double* __restrict__ out) {
     __shared__ double red[8];
@@ -396,6 +404,13 @@ cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const 
 cudaError_t small_gemm(const Launch& L, int B, const double* A, const double* X, double* Y, bool transA, double scale) {
     if (B < 1 || B > kBlockMax) return cudaErrorInvalidValue;
     k_small_gemm<<<B, kBlockMax, 0, L.stream>>>(B, A, X, Y, transA ? 1 : 0, scale);
+    count2(L);
+    return cudaGetLastError();
+}
+
+cudaError_t scale_rows(const Launch& L, int B, int N, const double* f, const float* X, float* Y) {
+    if (B <= 0) return cudaSuccess;
+    k_scale_rows<<<dim3((N + 1023) / 1024, B), 256, 0, L.stream>>>(B, N, f, X, Y);
     count2(L);
     return cudaGetLastError();
 }

@@ -95,6 +95,38 @@ def test_block_cg_many_frames_zero_frame_and_modes(T):
         T.tomo_destroy(h)
 
 
+@pytest.mark.parametrize("kappa", [1.0, 0.5])
+def test_block_cg_proportional_operators(T, kappa):
+    # four seeings in one block: nu_f = kappa c_f makes A_f = c_f (Sigma_ss + kappa Sigma_eta_eta)
+    cfg = small_cfg(n=7, lgs=True, obstruction=0.2, D=4.2, noise=0.15, targets=((0.0, 0.0), (10e-6, -5e-6)))
+    r0 = np.array([0.10, 0.133, 0.167, 0.20])
+    c = (r0 / cfg["r0"]) ** (-5.0 / 3.0)
+    nu = kappa * c
+    h = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=4, precond=True)
+    try:
+        info_l, _, _ = T.tomo_layout(h)
+        s = np.random.default_rng(6).standard_normal((4, info_l.N))
+        sd = torch.tensor(s, dtype=torch.float32, device="cuda")
+        zd = torch.zeros_like(sd)
+        phi = torch.empty((4, 2, info_l.n_vphi), dtype=torch.float32, device="cuda")
+        info = T.tomo_solve_r0(h, sd, 4, r0, T.solve_opts(tol=3e-5, max_iter=20000, max_refine=5, precond=True,
+                                                          method="block"), zd, phi, noise_scale=nu)
+        torch.cuda.synchronize()
+        z, phi = zd.double().cpu().numpy(), phi.double().cpu().numpy()
+        print("proportional block", info)
+        assert (info["status"] == 0).all() and (info["relres"] <= 3e-5).all()
+        sig2 = min(cfg["noise_sigma"]) ** 2
+        for f in range(4):
+            A = cov.system_matrix_r0(cfg, r0[f], nu[f])
+            zs = solve.solve_cholesky(A, s[f])
+            assert np.linalg.norm(z[f] - zs) <= info["relres"][f] * np.linalg.norm(s[f]) / (nu[f] * sig2)
+            for t in range(2):
+                ref = cov.cos_interp(dict(cfg, r0=r0[f]), t) @ zs
+                assert float(np.linalg.norm(phi[f, t] - ref) / np.linalg.norm(ref)) <= 2e-3
+    finally:
+        T.tomo_destroy(h)
+
+
 def test_block_cg_rejected_where_invalid(T):
     cfg = small_cfg(n=6, lgs=True)
     h = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=2)
@@ -102,7 +134,7 @@ def test_block_cg_rejected_where_invalid(T):
         info, _, _ = T.tomo_layout(h)
         sd = torch.ones((2, info.N), dtype=torch.float32, device="cuda")
         zd = torch.zeros_like(sd)
-        with pytest.raises(T.TomoError):        # per-frame operators: no common Krylov space
+        with pytest.raises(T.TomoError):        # fixed noise, two seeings: no common Krylov space
             T.tomo_solve_r0(h, sd, 2, np.array([0.1, 0.2]), T.solve_opts(method="block"), zd)
     finally:
         T.tomo_destroy(h)
