@@ -225,6 +225,21 @@ def dist_setup(use_cuda):
     return world, rank, local, dist if world > 1 else None
 
 
+def max_over_ranks(value, dist, device):
+    """The largest `value` over the ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, frames_per_rank, steps, max_ms):
+    """frames/s of the whole job: every rank's frames over the slowest rank's time."""
+    return world * frames_per_rank * steps / (max_ms / 1000.0)
+
+
 def workload(frames, seed):
     from paper_1806_07938_gb300 import workloads as W
     cfg = W.config("elt_ltao")
@@ -558,12 +573,8 @@ def run_ours(args):
                 learned_block = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, precond=True,
                                                         warm_start=2, method="block"),
                                         note="the same network as warm start of block PCG")
-        total_ms = sum(step_ms)
-        if dist:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-        value = world * F * args.steps / (total_ms / 1000.0)
+        total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+        value = whole_job_rate(world, F, args.steps, total_ms)
         info = infos[-1]
         iters = info["iters"]
         ok = bool((info["status"] == 0).all() and (info["relres"] <= TOL).all())
