@@ -999,33 +999,9 @@ void chol_drop(const std::vector<double>& A, int B, double rel_drop, std::vector
     }
 }
 
-// X = A^+ H for A = L L^T (dropped rows and columns excluded, their rows of X
-// zero); H, X [B][B]; scale multiplies the result.  Row-oriented: the inner
-// loops run over the B right-hand sides (contiguous, vectorised).
+// y -= a x over n contiguous entries (vectorised).
 inline void row_axpy(double* __restrict__ y, const double* __restrict__ x, double a, int n) {
     for (int c = 0; c < n; ++c) y[c] -= a * x[c];
-}
-
-void chol_solve(const std::vector<double>& L, const std::vector<char>& drop, int B, const std::vector<double>& H,
-                double scale, std::vector<double>& X) {
-    X = H;
-    double* Xd = X.data();
-    for (int i = 0; i < B; ++i) {
-        double* xi = Xd + (size_t)i * B;
-        if (drop[i]) { std::fill(xi, xi + B, 0.0); continue; }
-        for (int k = 0; k < i; ++k) row_axpy(xi, Xd + (size_t)k * B, L[(size_t)i * B + k], B);
-        const double inv = 1.0 / L[(size_t)i * B + i];
-        for (int c = 0; c < B; ++c) xi[c] *= inv;
-    }
-    for (int i = B - 1; i >= 0; --i) {
-        double* xi = Xd + (size_t)i * B;
-        if (drop[i]) continue;
-        for (int k = i + 1; k < B; ++k) row_axpy(xi, Xd + (size_t)k * B, L[(size_t)k * B + i], B);
-        const double inv = 1.0 / L[(size_t)i * B + i];
-        for (int c = 0; c < B; ++c) xi[c] *= inv;
-    }
-    if (scale != 1.0)
-        for (double& v : X) v *= scale;
 }
 
 // T = L^{-T} (upper triangular) with the dropped rows and columns of T zero,
