@@ -121,7 +121,9 @@ def fft_flops(L):
 
 
 def kernel_model(layout):
-    """Algorithmic flops and bytes per frame-iteration for each MVM pass (roofline section)."""
+    """Algorithmic flops and bytes per frame-iteration for each MVM pass: complex FFTs at 5 L log2 L
+    flops, 8 flops per complex multiply-add of the block product, and the vectors, half spectra and
+    spectra each pass must move."""
     n, P, NP, N = layout.n, layout.P, 2 * layout.n_gs, layout.N
     nh = P // 2 + 1
     rows_fft = NP * math.ceil(n / 2) * fft_flops(P)           # two real rows per complex FFT

@@ -68,7 +68,8 @@ def test_zero_lag_values(lgs):
 def test_paper_hudgin_formulas(lgs):
     # Appendix A.2: Sigma_sxsx = 1/2 [-2D(Delta) + D(Delta + d_x) + D(Delta - d_x)] and
     # Sigma_sxsy = 1/2 [D(Delta + d_x/2 + d_y/2) - D(Delta - d_x/2 + d_y/2) - D(Delta + d_x/2 - d_y/2)
-    #                    + D(Delta - d_x/2 - d_y/2)]   (the last sign corrected),
+    #                    + D(Delta - d_x/2 - d_y/2)]   (the paper prints the last sign as "-"; "+" is
+    #                    what the point-covariance derivation gives and Sigma_sxsy(0) = 0 requires),
     # Delta_k = gamma_k (c_a - c_b) + h_k (alpha_a - alpha_b), offsets gamma_k d (cone reading).
     cfg = small_cfg(n=5, lgs=lgs, obstruction=0.2)
     C = cov.css_dense(cfg)
