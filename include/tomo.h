@@ -100,7 +100,17 @@ typedef struct {
     double precond_floor;  /* c of the preconditioner (see tomo_solve_opts), 0 = 3 */
     int mode_removal;      /* 1: remove tip, tilt and focus (Sec. 2.F, mode
                               removal; see tomo_solve)                           */
+    int slope_model;       /* TOMO_SLOPE_HUDGIN (0) or TOMO_SLOPE_FRIED (1)         */
 } tomo_config;
+
+/* Slope model of the covariances (Appendix A; the paper compares both):
+ * Hudgin-like, a slope is the phase difference between the midpoints of the
+ * two subaperture edges across its direction; Fried, the mean of the
+ * differences along the two edges parallel to it, i.e. over the four corners
+ * with weights +-1/2 (it does not see the waffle mode of the corner grid).
+ * The model changes the generators and spectra only; tip, tilt and focus
+ * have the same slopes in both. */
+enum { TOMO_SLOPE_HUDGIN = 0, TOMO_SLOPE_FRIED = 1 };
 
 typedef struct {
     int n, n_gs, n_vs;     /* n_vs valid subapertures per WFS                     */

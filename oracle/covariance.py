@@ -43,10 +43,18 @@ def cone_factor(H, h):
 
 
 def slope_points(cfg):
-    """Per-slope pupil points and weights.
+    """Per-slope pupil points and weights of the slope model.
 
-    Returns (pts, w, gsidx): pts (N, 2, 2) = [slope][point][x|y] in metres,
-    w (N, 2) = +1 / -1, gsidx (N,) = guide-star index of each slope.
+    Hudgin-like (default, cfg["slope_model"] == "hudgin"; Appendix A.2): the
+    difference of the phase at the midpoints of the two edges across the
+    slope's direction, phi(c + d/2 e) - phi(c - d/2 e).  Fried: the mean of
+    that difference along the two other edges, i.e. over the four corners,
+    1/2 [phi(c + d/2 (e + f)) - phi(c - d/2 (e - f)) + phi(c + d/2 (e - f)) - phi(c - d/2 (e + f))]
+    with f the other axis (Appendix A: the Fried geometry on the corners).
+
+    Returns (pts, w, gsidx): pts (N, K, 2) = [slope][point][x|y] in metres
+    (K = 2 Hudgin, 4 Fried), w (N, K) the weights, gsidx (N,) the guide-star
+    index of each slope.
     """
     n, D, eps = cfg["n"], cfg["D"], cfg["obstruction"]
     d = D / n
@@ -54,13 +62,24 @@ def slope_points(cfg):
     pts, w, gi = [], [], []
     for g in range(len(cfg["gs"])):
         for comp in (0, 1):
-            off = np.zeros(2)
-            off[comp] = d / 2.0
+            off, wt = slope_stencil(cfg, comp, d)
             for cc in c:
-                pts.append([cc + off, cc - off])
-                w.append([1.0, -1.0])
+                pts.append([cc + o for o in off])
+                w.append(list(wt))
                 gi.append(g)
     return np.array(pts), np.array(w), np.array(gi, dtype=np.int64)
+
+
+def slope_stencil(cfg, comp, d):
+    """Offsets from the subaperture centre and weights of the points of one
+    slope component (0 = x, 1 = y) in the configuration's slope model."""
+    e = np.zeros(2)
+    e[comp] = d / 2.0
+    f = np.zeros(2)
+    f[1 - comp] = d / 2.0
+    if cfg.get("slope_model", "hudgin") == "fried":
+        return [e + f, -e + f, e - f, -e - f], (0.5, -0.5, 0.5, -0.5)
+    return [e, -e], (1.0, -1.0)
 
 
 def _layer_positions(cfg, pts, gsidx, k):
@@ -80,8 +99,9 @@ def css_rows(cfg, rows):
     for k, (h, frac) in enumerate(cfg["layers"]):
         r0k = turb.layer_r0(cfg["r0"], frac)
         pos = _layer_positions(cfg, pts, gsidx, k)
-        for u in (0, 1):
-            for v in (0, 1):
+        K = pts.shape[1]
+        for u in range(K):
+            for v in range(K):
                 diff = pos[rows, u][:, None, :] - pos[None, :, v, :]
                 rho = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
                 out += (w[rows, u][:, None] * w[None, :, v]) * turb.vk_covariance(rho, r0k, cfg["L0"])
@@ -134,7 +154,7 @@ def cos_exact(cfg, target):
         r0k = turb.layer_r0(cfg["r0"], frac)
         pos = _layer_positions(cfg, pts, gsidx, k)
         qk = q + h * np.array([bx, by])
-        for v in (0, 1):
+        for v in range(pts.shape[1]):
             diff = qk[:, None, :] - pos[None, :, v, :]
             rho = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
             out += w[None, :, v] * turb.vk_covariance(rho, r0k, cfg["L0"])
@@ -204,7 +224,7 @@ def cos_new_grid_layer(cfg, target, k):
     pts, w, gsidx = slope_points(cfg)
     pos = _layer_positions(cfg, pts, gsidx, k)
     out = np.zeros((len(nodes), len(pts)))
-    for v in (0, 1):
+    for v in range(pts.shape[1]):
         diff = nodes[:, None, :] - pos[None, :, v, :]
         rho = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
         out += w[None, :, v] * turb.vk_covariance(rho, r0k, cfg["L0"])
@@ -235,7 +255,7 @@ def cos_interp_rows(cfg, target, rows):
         r0k = turb.layer_r0(cfg["r0"], frac)
         pos = _layer_positions(cfg, pts, gsidx, k)
         X = np.zeros((len(used), len(pts)))
-        for v in (0, 1):
+        for v in range(pts.shape[1]):
             diff = nodes[:, None, :] - pos[None, :, v, :]
             rho = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
             X += w[None, :, v] * turb.vk_covariance(rho, r0k, cfg["L0"])

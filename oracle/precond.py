@@ -32,19 +32,17 @@ def periodised_generators(cfg, P):
         for q in range(NP):
             gi, ci = divmod(p, 2)
             gj, cj = divmod(q, 2)
-            oi = np.zeros(2)
-            oi[ci] = d / 2
-            oj = np.zeros(2)
-            oj[cj] = d / 2
+            oi, wi = cov.slope_stencil(cfg, ci, d)
+            oj, wj = cov.slope_stencil(cfg, cj, d)
             for (h, frac) in cfg["layers"]:
                 gam = cov.cone_factor(gs[gi][2], h)
                 r0k = turb.layer_r0(cfg["r0"], frac)
                 sh = h * (np.array(gs[gi][:2]) - np.array(gs[gj][:2]))
-                for su in (1, -1):
-                    for sv in (1, -1):
-                        dx = gam * (LX * d + su * oi[0] - sv * oj[0]) + sh[0]
-                        dy = gam * (LY * d + su * oi[1] - sv * oj[1]) + sh[1]
-                        t[p, q] += su * sv * turb.vk_covariance(np.hypot(dx, dy), r0k, cfg["L0"])
+                for ou, wu in zip(oi, wi):
+                    for ov, wv in zip(oj, wj):
+                        dx = gam * (LX * d + ou[0] - ov[0]) + sh[0]
+                        dy = gam * (LY * d + ou[1] - ov[1]) + sh[1]
+                        t[p, q] += wu * wv * turb.vk_covariance(np.hypot(dx, dy), r0k, cfg["L0"])
     return t
 
 

@@ -60,6 +60,7 @@ struct tomo_handle {
     int n = 0, n_gs = 0, NP = 0, n_vs = 0, N = 0, n_vphi = 0, n_layers = 0, n_targets = 0;
     int P = 0, Pc = 0, m = 0, cos_layers = 0, max_batch = 0;
     int rg = 1;                        // row groups per plane of the row passes (partial-sum layout)
+    int slope_model = TOMO_SLOPE_HUDGIN;
     int block_slots = 456;             // SMs x resident blocks of the row passes
     double D = 0, obstruction = 0, d = 0, r0 = 0, L0 = 0;
     bool all_ngs = true;
@@ -420,6 +421,7 @@ tomo_status validate(const tomo_config* c) {
         return TOMO_EINVAL;
     if (!(c->precond_floor >= 0)) return TOMO_EINVAL;
     if (c->mode_removal != 0 && c->mode_removal != 1) return TOMO_EINVAL;
+    if (c->slope_model != TOMO_SLOPE_HUDGIN && c->slope_model != TOMO_SLOPE_FRIED) return TOMO_EINVAL;
     if (c->max_batch < 1 || c->max_batch > 4096) return TOMO_EINVAL;
     const double H = c->gs[0].height;
     for (int g = 0; g < c->n_gs; ++g) {
@@ -535,6 +537,7 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     h->r0 = c->r0;
     h->L0 = c->L0;
     h->max_batch = c->max_batch;
+    h->slope_model = c->slope_model;
     h->all_ngs = c->gs[0].height == 0.0;
     const int n = h->n;
 
@@ -703,7 +706,7 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         TRY(dalloc(h, &h->d_K64, (size_t)npl * (h->P / 2 + 1) * h->P));
         TRY(dalloc(h, &h->d_K32, (size_t)(h->NP * (h->NP + 1) / 2) * (h->P / 2 + 1) * h->P));
         CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
-        CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G, false));
+        CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G, false, h->slope_model));
         CK(spectra(L, h->P, npl, h->NP, h->plan, G, H, h->d_tw64, h->d_K64, Kfull));
         CK(pack_hermitian(L, h->P, h->NP, Kfull, h->d_K32));
         CK(cudaStreamSynchronize(h->stream));
@@ -727,7 +730,7 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         TRY(dalloc(h, &h->d_zero_var, h->NP));
         CK(cudaMemsetAsync(h->d_zero_var, 0, sizeof(double) * h->NP, h->stream));
         CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
-        CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G, true));
+        CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G, true, h->slope_model));
         CK(spectra(L, h->P, npl, h->NP, h->plan, G, H, h->d_tw64, K64, nullptr));
         const double floor_c = c->precond_floor > 0 ? c->precond_floor : 3.0;
         CK(precond_spectra(L, h->P, h->NP, K64, h->d_noise_var, floor_c, Mfull));
@@ -751,7 +754,7 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         for (int t = 0; t < h->n_targets; ++t) {
             CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
             CK(gen_cos(L, n, h->m, h->Pc, h->NP, h->d, h->all_ngs ? -h->n_layers : h->n_layers, d_layers, d_alpha,
-                       c->target_x[t], c->target_y[t], vk, G));
+                       c->target_x[t], c->target_y[t], vk, G, h->slope_model));
             CK(spectra(L, h->Pc, npl, h->NP, h->planc, G, H, d_twc64, nullptr, h->d_Kc32 + t * kstride));
         }
         CK(cudaStreamSynchronize(h->stream));

@@ -1033,27 +1033,56 @@ __device__ double vk_shape(double x, const VkParams& vk) {
 // model, Appendix A.2; cone factor per layer, Sec. 2.D).  Stored at the
 // wrapped lag (di mod P, dj mod P) so that y = IFFT(FFT(t) FFT(x)) is the
 // linear convolution y(a) = sum_b t(a - b) x(b) on the n x n grid.
+// Points of one slope component (0 = x, 1 = y) relative to the subaperture
+// centre, and their weights, in the slope model (Appendix A): 0 Hudgin-like,
+// the midpoints of the two edges across the component, weights +1 / -1;
+// 1 Fried, the four corners, weights +-1/2 (the mean of the differences
+// along the two edges parallel to the component).
+struct Stencil {
+    int n;
+    double ox[4], oy[4], w[4];
+};
+
+__device__ __forceinline__ Stencil slope_stencil(int model, int comp, double d) {
+    const double h = 0.5 * d;
+    const double ex = comp == 0 ? h : 0.0, ey = comp == 1 ? h : 0.0;   // along the component
+    const double fx = comp == 0 ? 0.0 : h, fy = comp == 0 ? h : 0.0;   // across it
+    Stencil st;
+    if (model == 1) {
+        st.n = 4;
+        st.ox[0] = ex + fx;  st.oy[0] = ey + fy;  st.w[0] = 0.5;
+        st.ox[1] = -ex + fx; st.oy[1] = -ey + fy; st.w[1] = -0.5;
+        st.ox[2] = ex - fx;  st.oy[2] = ey - fy;  st.w[2] = 0.5;
+        st.ox[3] = -ex - fx; st.oy[3] = -ey - fy; st.w[3] = -0.5;
+    } else {
+        st.n = 2;
+        st.ox[0] = ex;  st.oy[0] = ey;  st.w[0] = 1.0;
+        st.ox[1] = -ex; st.oy[1] = -ey; st.w[1] = -1.0;
+        st.ox[2] = st.oy[2] = st.w[2] = st.ox[3] = st.oy[3] = st.w[3] = 0.0;
+    }
+    return st;
+}
+
 __global__ void k_gen_css(int lo, int span, int P, int NP, double d, int n_layers, const LayerGeom* __restrict__ layers,
-                          const double* __restrict__ alpha, VkParams vk, double* __restrict__ G) {
+                          const double* __restrict__ alpha, VkParams vk, int model, double* __restrict__ G) {
     const int li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= span * span) return;
     const int pair = blockIdx.y;
     const int p = pair / NP, q = pair % NP;
     const int gp = p >> 1, cp = p & 1, gq = q >> 1, cq = q & 1;
     const int di = li / span + lo, dj = li % span + lo;
-    const double opx = cp == 0 ? 0.5 * d : 0.0, opy = cp == 1 ? 0.5 * d : 0.0;
-    const double oqx = cq == 0 ? 0.5 * d : 0.0, oqy = cq == 1 ? 0.5 * d : 0.0;
+    const Stencil sp = slope_stencil(model, cp, d), sq = slope_stencil(model, cq, d);
     const double dax = alpha[2 * gp] - alpha[2 * gq], day = alpha[2 * gp + 1] - alpha[2 * gq + 1];
     const double k2pi = 2.0 * 3.14159265358979323846 / vk.L0;
     double t = 0.0;
     for (int k = 0; k < n_layers; ++k) {
         const LayerGeom lg = layers[k];
         double acc = 0.0;
-        for (int u = -1; u <= 1; u += 2)
-            for (int v = -1; v <= 1; v += 2) {
-                const double sx = lg.gamma * (dj * d + u * opx - v * oqx) + lg.h * dax;
-                const double sy = lg.gamma * (di * d + u * opy - v * oqy) + lg.h * day;
-                acc += (double)(u * v) * vk_shape(k2pi * sqrt(sx * sx + sy * sy), vk);
+        for (int u = 0; u < sp.n; ++u)
+            for (int v = 0; v < sq.n; ++v) {
+                const double sx = lg.gamma * (dj * d + sp.ox[u] - sq.ox[v]) + lg.h * dax;
+                const double sy = lg.gamma * (di * d + sp.oy[u] - sq.oy[v]) + lg.h * day;
+                acc += sp.w[u] * sq.w[v] * vk_shape(k2pi * sqrt(sx * sx + sy * sy), vk);
             }
         t += lg.amp * acc;
     }
@@ -1062,12 +1091,12 @@ __global__ void k_gen_css(int lo, int span, int P, int NP, double d, int n_layer
 }
 
 cudaError_t gen_css(const Launch& L, int n, int P, int NP, double d, int n_layers, const LayerGeom* layers,
-                    const double* gs_alpha, VkParams vk, double* G, bool periodised) {
+                    const double* gs_alpha, VkParams vk, double* G, bool periodised, int model) {
     // exact 2RBT generator: lags [-(n-1), n-1]; periodised: every lag of the P-torus, [-P/2, P/2)
     const int lo = periodised ? -(P / 2) : -(n - 1);
     const int span = periodised ? P : 2 * n - 1;
     k_gen_css<<<dim3((span * span + 127) / 128, NP * NP), 128, 0, L.stream>>>(lo, span, P, NP, d, n_layers, layers,
-                                                                            gs_alpha, vk, G);
+                                                                            gs_alpha, vk, model, G);
     count(L);
     return cudaGetLastError();
 }
@@ -1080,7 +1109,7 @@ cudaError_t gen_css(const Launch& L, int n, int P, int NP, double d, int n_layer
 // gamma = 1 for every layer and the interpolation is the identity).
 __global__ void k_gen_cos(int n, int m, int P, int NP, double d, int n_layers, int fold,
                           const LayerGeom* __restrict__ layers, const double* __restrict__ alpha, double bx, double by,
-                          VkParams vk, double* __restrict__ G) {
+                          VkParams vk, int model, double* __restrict__ G) {
     const int span = m + n - 1;
     const int li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= span * span) return;
@@ -1088,7 +1117,7 @@ __global__ void k_gen_cos(int n, int m, int P, int NP, double d, int n_layers, i
     const int kk = slot / NP, q = slot % NP;
     const int gq = q >> 1, cq = q & 1;
     const int di = li / span - (n - 1), dj = li % span - (n - 1);
-    const double oqx = cq == 0 ? 0.5 * d : 0.0, oqy = cq == 1 ? 0.5 * d : 0.0;
+    const Stencil sq = slope_stencil(model, cq, d);
     const double k2pi = 2.0 * 3.14159265358979323846 / vk.L0;
     const double half = 0.5 * (double)(n - m);
     double t = 0.0;
@@ -1096,10 +1125,10 @@ __global__ void k_gen_cos(int n, int m, int P, int NP, double d, int n_layers, i
     for (int k = k0; k < k1; ++k) {
         const LayerGeom lg = layers[k];
         double acc = 0.0;
-        for (int v = -1; v <= 1; v += 2) {
-            const double sx = lg.gamma * d * (dj + half) - v * lg.gamma * oqx + lg.h * (bx - alpha[2 * gq]);
-            const double sy = lg.gamma * d * (di + half) - v * lg.gamma * oqy + lg.h * (by - alpha[2 * gq + 1]);
-            acc += (double)v * vk_shape(k2pi * sqrt(sx * sx + sy * sy), vk);
+        for (int v = 0; v < sq.n; ++v) {
+            const double sx = lg.gamma * (d * (dj + half) - sq.ox[v]) + lg.h * (bx - alpha[2 * gq]);
+            const double sy = lg.gamma * (d * (di + half) - sq.oy[v]) + lg.h * (by - alpha[2 * gq + 1]);
+            acc += sq.w[v] * vk_shape(k2pi * sqrt(sx * sx + sy * sy), vk);
         }
         t += lg.amp * acc;
     }
@@ -1108,13 +1137,13 @@ __global__ void k_gen_cos(int n, int m, int P, int NP, double d, int n_layers, i
 }
 
 cudaError_t gen_cos(const Launch& L, int n, int m, int P, int NP, double d, int n_layers, const LayerGeom* layers,
-                    const double* gs_alpha, double bx, double by, VkParams vk, double* G) {
+                    const double* gs_alpha, double bx, double by, VkParams vk, double* G, int model) {
     // n_layers < 0 requests the folded (single-slot) form
     const int fold = n_layers < 0 ? 1 : 0;
     const int nl = fold ? -n_layers : n_layers;
     const int span = m + n - 1;
     k_gen_cos<<<dim3((span * span + 127) / 128, (fold ? 1 : nl) * NP), 128, 0, L.stream>>>(
-        n, m, P, NP, d, nl, fold, layers, gs_alpha, bx, by, vk, G);
+        n, m, P, NP, d, nl, fold, layers, gs_alpha, bx, by, vk, model, G);
     count(L);
     return cudaGetLastError();
 }

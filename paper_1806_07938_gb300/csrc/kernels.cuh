@@ -222,8 +222,10 @@ struct LayerGeom {
 // Sigma_ss generators on the wrapped P x P grid: G[p*NP+q][P][P] (pre-zeroed).
 // periodised = false: the exact 2RBT generator, lags [-(n-1), n-1];
 // periodised = true: the covariance at every lag of the P-torus, [-P/2, P/2).
+// model: slope model of the points (0 Hudgin-like, 1 Fried).
 cudaError_t gen_css(const Launch& L, int n, int P, int NP, double d, int n_layers,
-                    const LayerGeom* layers, const double* gs_alpha, VkParams vk, double* G, bool periodised);
+                    const LayerGeom* layers, const double* gs_alpha, VkParams vk, double* G, bool periodised,
+                    int model);
 // Block-circulant preconditioner spectra M(f) = (K_+(f) + c diag(sigma^2))^{-1} / P^2
 // from the FP64 spectra of the periodised generator (both [nh][NP][P][NP]).
 cudaError_t precond_spectra(const Launch& L, int P, int NP, const double2* K64, const double* noise_var,
@@ -231,7 +233,7 @@ cudaError_t precond_spectra(const Launch& L, int P, int NP, const double2* K64, 
 // Sigma_phi_s generators of one target: G[k*NP+q][P][P] for the m x n 2RBT blocks.
 cudaError_t gen_cos(const Launch& L, int n, int m, int P, int NP, double d, int n_layers,
                     const LayerGeom* layers, const double* gs_alpha, double bx, double by,
-                    VkParams vk, double* G);
+                    VkParams vk, double* G, int model);
 // Spectra: 2-D real FFT of each G plane, scaled by 1/P^2, into
 // K [nh][NPin][P][NPout] (plane index p*NPin + q), FP64 and FP32 copies.
 cudaError_t spectra(const Launch& L, int P, int npl, int NPin, const FftPlan& plan,

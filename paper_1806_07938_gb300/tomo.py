@@ -32,7 +32,8 @@ class tomo_config(ctypes.Structure):
                 ("n_targets", ctypes.c_int), ("target_x", ctypes.POINTER(ctypes.c_double)),
                 ("target_y", ctypes.POINTER(ctypes.c_double)),
                 ("fft_P", ctypes.c_int), ("fft_Pcos", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("precond", ctypes.c_int), ("precond_floor", ctypes.c_double), ("mode_removal", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("precond_floor", ctypes.c_double), ("mode_removal", ctypes.c_int),
+                ("slope_model", ctypes.c_int)]
 
 
 class tomo_layout_info(ctypes.Structure):
@@ -152,7 +153,7 @@ def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_fl
     ty = (ctypes.c_double * nt)(*[t[1] for t in cfg["targets"]])
     c = tomo_config(cfg["D"], cfg["obstruction"], cfg["n"], n_gs, gs, nl, lh, lf, cfg["r0"], cfg["L0"],
                     nt, tx, ty, fft_P, fft_Pcos, max_batch, int(bool(precond)), float(precond_floor),
-                    int(bool(mode_removal)))
+                    int(bool(mode_removal)), SLOPE_MODELS[cfg.get("slope_model", "hudgin")])
     c._keep = (gs, lh, lf, tx, ty)
     return c
 
@@ -213,6 +214,7 @@ def tomo_apply_cos(h, zeta, phase, batch):
 
 
 METHODS = {"cg": 0, "minres": 1, "block": 2}
+SLOPE_MODELS = {"hudgin": 0, "fried": 1}
 
 
 def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=0, check_every=32, precond=False, method="cg"):

@@ -158,6 +158,30 @@ def test_row_group_split_matches_oracle(T):
             assert (np.linalg.norm(z - zs, axis=1) <= bound).all()
 
 
+@pytest.mark.parametrize("lgs,pcg", [(False, False), (True, True)])
+def test_fried_model_matches_oracle(T, lgs, pcg):
+    # the Fried slope model (four corners, weights +-1/2): product, projection
+    # and solve against the oracle's point covariances
+    cfg = dict(small_cfg(n=9, lgs=lgs, obstruction=0.2, D=4.5, noise=0.15, targets=((0.0, 0.0), (12e-6, 4e-6))),
+               slope_model="fried")
+    A = cov.system_matrix(cfg)
+    x = np.random.default_rng(17).standard_normal((3, A.shape[0]))
+    with Handle(T, cfg, max_batch=2, precond=pcg) as H:
+        assert relL2(H.css(x), x @ A.T) <= 1e-5
+        assert relL2(H.css(x, f64=True), x @ A.T) <= 1e-11
+        y = H.cos(x[:2])
+        for t in range(2):
+            assert relL2(y[:, t], x[:2] @ cov.cos_interp(cfg, t).T) <= 1e-5
+        # the Fried model leaves the waffle mode to the noise term: cond(A) is
+        # 4.4e4 here and storing the exact solution in FP32 already leaves a
+        # relative residual of 6e-5 to 9e-5, so the solve is checked at 2.5e-4
+        z, _, info = H.solve(x, tol=2.5e-4, max_iter=20000, max_refine=5, precond=pcg)
+        assert (info["status"] == 0).all() and (info["relres"] <= 2.5e-4).all()
+        zs = solve.solve_cholesky(A, x.T).T
+        bound = info["relres"] * np.linalg.norm(x, axis=1) / 0.15 ** 2
+        assert (np.linalg.norm(z - zs, axis=1) <= bound).all()
+
+
 def test_css_zero_and_empty(T):
     cfg = small_cfg(n=6, lgs=True)
     with Handle(T, cfg, max_batch=2) as H:
