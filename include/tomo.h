@@ -36,6 +36,9 @@
  * spectra, tables and workspaces.  Device-pointer entry points enqueue work on
  * the handle's stream and return without synchronising; *_host entry points
  * copy in, run and copy out, and return after the stream has finished.
+ * Solves also synchronise their own private stream at each convergence check.
+ * A handle keeps per-call workspaces: use it from one host thread at a time
+ * (separate handles are independent, on one device or several). 
  *
  * Errors: every call returns a tomo_status; on failure nothing is written to
  * the outputs that the caller can rely on.  Per-frame non-convergence is not
