@@ -125,20 +125,50 @@ def noise_variance(cfg):
     return sig[gsidx] ** 2
 
 
+def add_noise(A, cfg, scale=1.0):
+    """A += scale * Sigma_eta_eta on valid slopes, in place.
+
+    Without ``cfg["noise_cov"]`` the noise is white per guide star: the
+    diagonal sigma_g^2 (Sec. 2.B).  With it (elongated laser spots, Sec. 2.F)
+    Sigma_eta_eta is block diagonal with one 2 x 2 block per subaperture:
+    ``noise_cov[g][i][j] = (s_xx, s_yy, s_xy)`` is the covariance of the x- and
+    y-slope noise of subaperture (i, j) of guide star g, whose two slopes sit at
+    rows off_g + e and off_g + n_valid + e (e its row-major valid index)."""
+    C = cfg.get("noise_cov")
+    if C is None:
+        A[np.diag_indices_from(A)] += scale * noise_variance(cfg)
+        return A
+    C = np.asarray(C, dtype=np.float64)
+    valid = geo.valid_list(geo.subaperture_mask(cfg["n"], cfg["obstruction"]))
+    nv = len(valid)
+    for g in range(len(cfg["gs"])):
+        for e, (i, j) in enumerate(valid):
+            sxx, syy, sxy = C[g, i, j]
+            ix = 2 * g * nv + e
+            iy = ix + nv
+            A[ix, ix] += scale * sxx
+            A[iy, iy] += scale * syy
+            A[ix, iy] += scale * sxy
+            A[iy, ix] += scale * sxy
+    return A
+
+
+def noise_matrix(cfg):
+    """Dense Sigma_eta_eta on valid slopes (see add_noise)."""
+    N = len(noise_variance(cfg))
+    return add_noise(np.zeros((N, N)), cfg)
+
+
 def system_matrix(cfg):
     """A = W_s (Sigma_ss + Sigma_eta_eta) W_s^T on valid slopes (Eq. SAap1)."""
-    A = css_dense(cfg)
-    A[np.diag_indices_from(A)] += noise_variance(cfg)
-    return A
+    return add_noise(css_dense(cfg), cfg)
 
 
 def system_matrix_r0(cfg, r0, noise_scale=1.0):
     """A of a frame seen with Fried parameter r0 (same Cn^2 fractions): Sigma_ss
     formed at that r0 from the point covariances, plus noise_scale times the
     configuration's noise variance (Eq. SAap1 for that frame)."""
-    A = css_dense(dict(cfg, r0=float(r0)))
-    A[np.diag_indices_from(A)] += float(noise_scale) * noise_variance(cfg)
-    return A
+    return add_noise(css_dense(dict(cfg, r0=float(r0))), cfg, float(noise_scale))
 
 
 def cos_exact(cfg, target):

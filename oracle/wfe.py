@@ -38,7 +38,7 @@ def analytic_wfe(cfg, target=0, R=None, A=None):
     """Mean square piston-removed error per phase point [rad^2], Eq. analytical1-3."""
     F = cov.cos_interp(cfg, target)
     Css = cov.css_dense(cfg)
-    Ceta = np.diag(cov.noise_variance(cfg))
+    Ceta = cov.noise_matrix(cfg)
     if R is None:
         R = solve.reconstructor(F, Css + Ceta if A is None else A)
     Cpp = phase_covariance(cfg)

@@ -37,6 +37,13 @@ rigidly with its wind vector, so step t samples the screen at x - v t dt; the
 screens of a sequence are drawn once, the noise anew at every step.  The wind
 profile is synthetic as well (the paper gives none).
 
+Elongated laser spots (``elongated_noise``, Sec. 2.F): a synthetic side-launch
+model.  The launch telescope of laser star g sits at radius 0.55 D on the star's
+azimuth; a subaperture at pupil position p sees the spot stretched along
+u = (p - launch) / |p - launch|, so its slope noise covariance is
+sigma^2 (I + (k |p - launch| / D)^2 u u^T) with k the elongation at one
+pupil diameter.  Natural stars (H = 0) keep sigma^2 I.
+
 Slopes are returned on the full n x n subaperture grid,
 ``[frame][gs][x|y][i][j]``; callers select the valid subapertures with the mask
 of the side they exercise.
@@ -272,6 +279,31 @@ def slope_frames_parallel(cfg, n_frames, seed=0, workers=None, chunk=8):
     with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
         parts = list(ex.map(_frames_job, jobs))
     return np.concatenate([p[0] for p in parts]), parts[0][1]
+
+
+def elongated_noise(cfg, sigma, k=2.0):
+    """Per-subaperture 2 x 2 slope noise covariances [n_gs][n][n][3] (s_xx, s_yy,
+    s_xy) of the side-launch elongation model above; ``sigma`` is one value or
+    one per guide star."""
+    n, D = cfg["n"], cfg["D"]
+    d = D / n
+    sig = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (len(cfg["gs"]),))
+    c = (np.arange(n) + 0.5) * d - D / 2
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    out = np.zeros((len(cfg["gs"]), n, n, 3))
+    for g, (ax, ay, H) in enumerate(cfg["gs"]):
+        s2 = sig[g] ** 2
+        out[g, :, :, 0] = s2
+        out[g, :, :, 1] = s2
+        if H <= 0:
+            continue
+        th = math.atan2(ay, ax)
+        vx, vy = X - 0.55 * D * math.cos(th), Y - 0.55 * D * math.sin(th)
+        e2 = (k / D) ** 2                                  # (k |v| / D)^2 u u^T = e2 v v^T
+        out[g, :, :, 0] += s2 * e2 * vx * vx
+        out[g, :, :, 1] += s2 * e2 * vy * vy
+        out[g, :, :, 2] = s2 * e2 * vx * vy
+    return out
 
 
 def warm_start_init(n_planes, hidden, seed, last_gain=0.1):

@@ -1,0 +1,86 @@
+"""Pins of the oracle's elongated-spot noise covariance (Sec. 2.F): one 2 x 2
+block per subaperture coupling its x- and y-slope noise."""
+import numpy as np
+
+from conftest import small_cfg
+from oracle import covariance as cov
+from oracle import geometry as geo
+from paper_1806_07938_gb300 import workloads as W
+
+
+def elongated(n=6, k=3.0, sigma=0.15, lgs=True):
+    cfg = small_cfg(n=n, lgs=lgs, obstruction=0.2, D=0.6 * n, noise=sigma)
+    cfg["noise_cov"] = W.elongated_noise(cfg, sigma, k)
+    return cfg
+
+
+def test_block_noise_matches_sampled_noise():
+    # draw slope noise on the full grid [g][x|y][i][j] from each subaperture's
+    # 2 x 2 covariance (explicit 2 x 2 Cholesky factor), select the valid
+    # subapertures as the slope vector is laid out, and compare the sample
+    # covariance with the oracle's matrix entry by entry (6 standard errors)
+    cfg = elongated()
+    S = cov.noise_matrix(cfg)
+    mask = geo.subaperture_mask(cfg["n"], cfg["obstruction"])
+    C = cfg["noise_cov"]
+    a, b, c = C[..., 0], C[..., 2], C[..., 1]
+    l11 = np.sqrt(a)
+    l21 = b / l11
+    l22 = np.sqrt(c - l21 ** 2)
+    rng = np.random.default_rng(2024)
+    M, chunk = 200_000, 20_000
+    acc = np.zeros_like(S)
+    for _ in range(M // chunk):
+        u = rng.standard_normal((chunk, 2) + C.shape[:3])           # [m][2][g][i][j]
+        ex = l11 * u[:, 0]
+        ey = l21 * u[:, 0] + l22 * u[:, 1]
+        eta = np.stack([ex, ey], axis=2)                            # [m][g][x|y][i][j]
+        v = eta[..., mask].reshape(chunk, -1)
+        acc += v.T @ v
+    E = acc / M
+    d = np.diag(S)
+    se = np.sqrt((np.outer(d, d) + S ** 2) / M)
+    assert np.abs(E - S).max() > 0                                  # the comparison is live
+    assert (np.abs(E - S) <= 6 * se).all()
+    # the cross terms are resolved: the largest |s_xy| is many standard errors
+    assert np.abs(S - np.diag(d)).max() > 50 * se.max()
+
+
+def test_isotropic_blocks_reduce_to_white_noise():
+    # no elongation (k = 0), and natural stars at any k: sigma^2 I
+    for cfg in (elongated(k=0.0), elongated(k=3.0, lgs=False)):
+        S = cov.noise_matrix(cfg)
+        assert np.array_equal(S, np.diag(cov.noise_variance(dict(cfg, noise_cov=None))))
+        A = cov.system_matrix(cfg)
+        assert np.array_equal(A, cov.system_matrix(dict(cfg, noise_cov=None)))
+
+
+def test_block_noise_structure():
+    cfg = elongated(n=7)
+    S = cov.noise_matrix(cfg)
+    nv = int(geo.subaperture_mask(7, 0.2).sum())
+    assert np.array_equal(S, S.T)
+    # each row couples only the slope of the other axis in its own subaperture
+    off = S - np.diag(np.diag(S))
+    rows, cols = np.nonzero(off)
+    assert (np.abs(rows - cols) == nv).all()
+    assert (rows // (2 * nv) == cols // (2 * nv)).all()
+    # smallest eigenvalue sigma^2 (the side-launch blocks are sigma^2 (I + e^2 v v^T))
+    assert abs(np.linalg.eigvalsh(S).min() - 0.15 ** 2) <= 1e-12
+    # r0 / noise-scaled system: Sigma_ss(r0) + nu Sigma_eta_eta
+    A = cov.system_matrix_r0(cfg, 0.1, noise_scale=2.5)
+    assert np.abs(A - cov.css_dense(dict(cfg, r0=0.1)) - 2.5 * S).max() <= 1e-14 * np.abs(A).max()
+
+
+def test_noise_weighted_reconstructor_is_optimal():
+    # the MMSE reconstructor built with the true (block) noise has a smaller
+    # mean square error under that noise than one built assuming white noise
+    # (Eq. analytical1 evaluated for both with the true covariances)
+    from oracle import solve, wfe
+    cfg = small_cfg(n=8, lgs=True, obstruction=0.2, D=4.8, noise=0.3, targets=((0.0, 0.0),))
+    cfg["noise_cov"] = W.elongated_noise(cfg, 0.3, 4.0)
+    best = wfe.analytic_wfe(cfg, 0)
+    F = cov.cos_interp(cfg, 0)
+    R_white = solve.reconstructor(F, cov.system_matrix(dict(cfg, noise_cov=None)))
+    mismatched = wfe.analytic_wfe(cfg, 0, R=R_white)
+    assert mismatched > best * (1 + 1e-3)
