@@ -104,6 +104,15 @@ typedef struct {
     int mode_removal;      /* 1: remove tip, tilt and focus (Sec. 2.F, mode
                               removal; see tomo_solve)                           */
     int slope_model;       /* TOMO_SLOPE_HUDGIN (0) or TOMO_SLOPE_FRIED (1)         */
+    const double* noise_cov;   /* NULL, or [n_gs][n][n][3] = s_xx, s_yy, s_xy:
+                              per subaperture (row-major grid; entries outside
+                              the pupil are ignored) the 2 x 2 covariance of its
+                              x and y slope noise (elongated laser spots,
+                              Sec. 2.F).  It replaces noise_sigma in
+                              Sigma_eta_eta; noise_sigma still sets the
+                              preconditioner's floor.  Each valid block must be
+                              positive semidefinite (TOMO_EINVAL otherwise).
+                              Read during tomo_create only. */
 } tomo_config;
 
 /* Slope model of the covariances (Appendix A; the paper compares both):
@@ -203,7 +212,9 @@ tomo_status tomo_layout(const tomo_handle* h, tomo_layout_info* info,
                         uint8_t* subap_mask, uint8_t* phase_mask);
 
 /* y = W_s (Sigma_ss + Sigma_eta_eta) W_s^T x for `batch` frames, FP32 through
- * the 2RBT MVM (Eq. mvm_ss plus the diagonal noise term of Eq. SAap1).
+ * the 2RBT MVM (Eq. mvm_ss plus the noise term of Eq. SAap1: diagonal, or with
+ * cfg.noise_cov the 2 x 2 per-subaperture blocks of Sec. 2.F, applied by a
+ * separate pass over each guide star's slopes).
  * x_dev, y_dev: device [batch][N] floats, must not alias. */
 tomo_status tomo_apply_css(tomo_handle* h, const float* x_dev, float* y_dev, int batch);
 

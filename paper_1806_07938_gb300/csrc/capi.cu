@@ -61,6 +61,8 @@ struct tomo_handle {
     int P = 0, Pc = 0, m = 0, cos_layers = 0, max_batch = 0;
     int rg = 1;                        // row groups per plane of the row passes (partial-sum layout)
     int slope_model = TOMO_SLOPE_HUDGIN;
+    double* d_ncov = nullptr;          // elongated-spot noise blocks [n_gs][n_vs][3] (nullptr: diagonal noise)
+    double* d_rows_noise = nullptr;    // the diagonal the row-inverse pass adds (zero with d_ncov)
     int block_slots = 456;             // SMs x resident blocks of the row passes
     double D = 0, obstruction = 0, d = 0, r0 = 0, L0 = 0;
     bool all_ngs = true;
@@ -255,8 +257,10 @@ tomo_status apply_ss32(tomo_handle* h, const Launch& L, const float* x, float* y
     CK((cols_mul<float>(L, h->g_ss, B, st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
     const float* xin = cg ? cg->p : x;
     float* yout = cg ? cg->Ap : y;
-    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, st, h->Y1, xin, h->d_noise_var, fscale, yout, cg,
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, st, h->Y1, xin, h->d_rows_noise, fscale, yout, cg,
                                       h->d_tw32, rg)));
+    if (h->d_ncov)
+        CK(noise_blocks<float>(L, B, h->n_vs, h->n_gs, rg, h->d_ncov, fscale, st, yout, xin, xin, cg));
     return TOMO_OK;
 }
 
@@ -269,8 +273,10 @@ tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double*
     const int rg = rg_for(h, B);
     CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1d, h->d_tw64, rg)));
     CK((cols_mul<double>(L, h->g_ss, B, nullptr, h->X1d, h->Y1d, h->d_K64, h->d_tw64, false)));
-    CK((rows_inv_masked<double, double>(L, h->g_ss, h->mt, B, nullptr, h->Y1d, x, h->d_noise_var, fscale, y,
+    CK((rows_inv_masked<double, double>(L, h->g_ss, h->mt, B, nullptr, h->Y1d, x, h->d_rows_noise, fscale, y,
                                         nullptr, h->d_tw64, rg)));
+    if (h->d_ncov)
+        CK(noise_blocks<double>(L, B, h->n_vs, h->n_gs, rg, h->d_ncov, fscale, nullptr, y, x, nullptr, nullptr));
     return TOMO_OK;
 }
 
@@ -324,8 +330,10 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, int kind, std::vec
         TRY(mark(0));
         CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
         TRY(mark(1));
-        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->r, h->d_noise_var, h->d_fscale,
+        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->r, h->d_rows_noise, h->d_fscale,
                                           h->w, &cg, h->d_tw32, rg)));
+        if (h->d_ncov)
+            CK(noise_blocks<float>(L, B, h->n_vs, h->n_gs, rg, h->d_ncov, h->d_fscale, h->st, h->w, h->r, h->r, &cg));
         if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, rg, h->d_Qs, h->st, h->w, h->r, &cg));
         TRY(mark(2));
         CK(mr_scalars(L, B, h->NP * rg, h->rr_part, h->dot_part, h->st));
@@ -338,8 +346,10 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, int kind, std::vec
         TRY(mark(0));
         CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
         TRY(mark(1));
-        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_noise_var, h->d_fscale,
+        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->p, h->d_rows_noise, h->d_fscale,
                                           h->Ap, &cg, h->d_tw32, rg)));
+        if (h->d_ncov)
+            CK(noise_blocks<float>(L, B, h->n_vs, h->n_gs, rg, h->d_ncov, h->d_fscale, h->st, h->Ap, h->p, h->p, &cg));
         if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, rg, h->d_Qs, h->st, h->Ap, h->p, &cg));
         TRY(mark(2));
         CK(cg_scalars(L, B, h->NP * rg, h->rr_part, h->dot_part, h->st));
@@ -360,8 +370,10 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, int kind, std::vec
     TRY(mark(0));
     CK((cols_mul<float>(L, h->g_ss, B, h->st, h->X1, h->Y1, h->d_K32, h->d_tw32, true)));
     TRY(mark(1));
-    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->z, h->d_noise_var, h->d_fscale,
+    CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, h->st, h->Y1, h->z, h->d_rows_noise, h->d_fscale,
                                       h->w, &cgA, h->d_tw32, rg)));
+    if (h->d_ncov)
+        CK(noise_blocks<float>(L, B, h->n_vs, h->n_gs, rg, h->d_ncov, h->d_fscale, h->st, h->w, h->z, h->z, &cgA));
     if (h->modes) CK(mode_project<float>(L, B, 2 * h->n_vs, h->n_gs, rg, h->d_Qs, h->st, h->w, h->z, &cgA));
     TRY(mark(2));
     CK(pcg_scalars(L, B, h->NP * rg, h->rr_part, h->dot_part_M, h->dot_part, h->st));
@@ -646,6 +658,27 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
     for (int p = 0; p < h->NP; ++p) nvar[p] = c->gs[p / 2].noise_sigma * c->gs[p / 2].noise_sigma;
     TRY(dalloc(h, &h->d_noise_var, h->NP));
     TRY(upload(h, nvar.data(), h->d_noise_var, sizeof(double) * h->NP));
+    h->d_rows_noise = h->d_noise_var;
+    if (c->noise_cov) {
+        // gather the valid subapertures' blocks: [n_gs][n][n][3] -> [n_gs][n_vs][3]
+        const size_t nc = (size_t)h->n_gs * h->n_vs * 3;
+        std::vector<double> blocks(nc);
+        for (int g = 0; g < h->n_gs; ++g)
+            for (int i = 0; i < n; ++i)
+                for (int e = rowstart[i]; e < rowstart[i + 1]; ++e) {
+                    const double* src = c->noise_cov + (((size_t)g * n + i) * n + col[e]) * 3;
+                    const double a = src[0], b = src[1], x = src[2];
+                    if (!(a >= 0) || !(b >= 0) || !std::isfinite(a) || !std::isfinite(b) || !std::isfinite(x) ||
+                        !(a * b - x * x >= 0))
+                        return TOMO_EINVAL;
+                    std::memcpy(&blocks[((size_t)g * h->n_vs + e) * 3], src, 3 * sizeof(double));
+                }
+        TRY(dalloc(h, &h->d_ncov, nc));
+        TRY(upload(h, blocks.data(), h->d_ncov, sizeof(double) * nc));
+        const std::vector<double> zero(h->NP, 0.0);
+        TRY(dalloc(h, &h->d_rows_noise, h->NP));
+        TRY(upload(h, zero.data(), h->d_rows_noise, sizeof(double) * h->NP));
+    }
 
     // --- FFT sides and plans ----------------------------------------------------------
     if (c->fft_P < 0) TRY(autotune_side(h));
@@ -1415,8 +1448,10 @@ tomo_status tomo_apply_css_noalloc(tomo_handle* h, const float* x, float* y, int
         float* yb = y + (size_t)f0 * h->N;
         CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, xb, nullptr, nullptr, X1, h->d_tw32)));
         CK((cols_mul<float>(L, h->g_ss, B, nullptr, X1, Y1, h->d_K32, h->d_tw32, true)));
-        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, nullptr, Y1, xb, h->d_noise_var, nullptr, yb,
+        CK((rows_inv_masked<float, float>(L, h->g_ss, h->mt, B, nullptr, Y1, xb, h->d_rows_noise, nullptr, yb,
                                           nullptr, h->d_tw32)));
+        if (h->d_ncov)
+            CK(noise_blocks<float>(L, B, h->n_vs, h->n_gs, 1, h->d_ncov, nullptr, nullptr, yb, xb, nullptr, nullptr));
     }
     return TOMO_OK;
 }

@@ -169,6 +169,14 @@ template <typename TV>
 cudaError_t mode_project(const Launch& L, int B, int len, int nblk, int rg, const double* Q, const FrameState* st,
                          TV* y, const float* xin, const CgVecs* cg);
 
+// Elongated-spot noise (modes.cu): y += nu_f Sigma_eta_eta x with one 2 x 2
+// block per subaperture (cov [n_gs][n_vs][3] = s_xx, s_yy, s_xy; nu_f =
+// fscale[f].y or 1), x and y [B][n_gs][2][n_vs]; with cg the partial sums of
+// the updated y replace those of the row-inverse pass (as mode_project).
+template <typename TV>
+cudaError_t noise_blocks(const Launch& L, int B, int n_vs, int n_gs, int rg, const double* cov, const double2* fscale,
+                         const FrameState* st, TV* y, const TV* x, const float* xin, const CgVecs* cg);
+
 // --- adjoint projection and explicit reconstructor (recon.cu) -----------------
 // out [B][n_layers][m][m] = I'^T of phi[:, t, :] through the transposed
 // bilinear table (ptr [n_layers][m*m + 1], vi / w entries: phase point, weight).

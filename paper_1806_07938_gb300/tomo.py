@@ -33,7 +33,7 @@ class tomo_config(ctypes.Structure):
                 ("target_y", ctypes.POINTER(ctypes.c_double)),
                 ("fft_P", ctypes.c_int), ("fft_Pcos", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("precond", ctypes.c_int), ("precond_floor", ctypes.c_double), ("mode_removal", ctypes.c_int),
-                ("slope_model", ctypes.c_int)]
+                ("slope_model", ctypes.c_int), ("noise_cov", ctypes.POINTER(ctypes.c_double))]
 
 
 class tomo_layout_info(ctypes.Structure):
@@ -151,10 +151,16 @@ def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_fl
     nt = len(cfg["targets"])
     tx = (ctypes.c_double * nt)(*[t[0] for t in cfg["targets"]])
     ty = (ctypes.c_double * nt)(*[t[1] for t in cfg["targets"]])
+    ncov = cfg.get("noise_cov")
+    if ncov is not None:
+        ncov = np.ascontiguousarray(ncov, dtype=np.float64)
+        if ncov.shape != (n_gs, cfg["n"], cfg["n"], 3):
+            raise ValueError("noise_cov must be [n_gs][n][n][3]")
     c = tomo_config(cfg["D"], cfg["obstruction"], cfg["n"], n_gs, gs, nl, lh, lf, cfg["r0"], cfg["L0"],
                     nt, tx, ty, fft_P, fft_Pcos, max_batch, int(bool(precond)), float(precond_floor),
-                    int(bool(mode_removal)), SLOPE_MODELS[cfg.get("slope_model", "hudgin")])
-    c._keep = (gs, lh, lf, tx, ty)
+                    int(bool(mode_removal)), SLOPE_MODELS[cfg.get("slope_model", "hudgin")],
+                    None if ncov is None else ncov.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    c._keep = (gs, lh, lf, tx, ty, ncov)
     return c
 
 

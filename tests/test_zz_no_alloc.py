@@ -42,3 +42,28 @@ def test_noalloc_matches_apply_css_twice():
         assert np.linalg.norm(o - g["y"]) / np.linalg.norm(g["y"]) <= 1e-5
     finally:
         tomo.tomo_destroy(h)
+
+
+def test_noalloc_with_elongated_noise():
+    # the 2 x 2 noise blocks of elongated laser spots (Sec. 2.F) on the same path
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from conftest import small_cfg
+    from oracle import covariance as cov
+    from paper_1806_07938_gb300 import tomo
+    from paper_1806_07938_gb300 import workloads as W
+    cfg = small_cfg(n=9, lgs=True, obstruction=0.2, D=5.4, noise=0.15)
+    cfg["noise_cov"] = W.elongated_noise(cfg, 0.15, 3.0)
+    A = cov.system_matrix(cfg)
+    x = np.random.default_rng(9).standard_normal((2, A.shape[0]))
+    h = tomo.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=2)
+    try:
+        xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+        out = torch.full_like(xd, float("nan"))
+        tomo.tomo_apply_css_noalloc(h, xd, out, 2)
+        torch.cuda.synchronize()
+        o = out.double().cpu().numpy()
+        ref = x @ A.T
+        assert np.linalg.norm(o - ref) / np.linalg.norm(ref) <= 1e-5
+    finally:
+        tomo.tomo_destroy(h)
