@@ -153,6 +153,70 @@ __device__ __forceinline__ void gstage(C* base, int gstride, const C* __restrict
     __syncwarp();
 }
 
+// The same stage over count <= GG sequences, one round of whole sequences at a
+// time: a round gives SPR = floor(32 / (P / R)) sequences one lane per
+// butterfly, reads, synchronises the warp and writes back.  As no sequence
+// spans two rounds, only one round's data is held in registers (the stage
+// above keeps all of them across its single synchronisation), so large groups
+// cost no registers; for 150 = 15 x 10 a group of six fills 30 of 32 lanes in
+// both stages (rounds of three and of two sequences).  Sequences >= count are
+// skipped.
+template <typename C, int P, int GG, int Ns, int R, bool FWD, bool LAST>
+__device__ __forceinline__ void cstage(C* base, int gstride, int count, const C* __restrict__ tw, int lane, int nin,
+                                       int nout) {
+    constexpr int PR = P / R;
+    static_assert(PR <= 32, "one sequence's butterflies must fit a warp");
+    constexpr int SPR = 32 / PR;
+    constexpr int tstep = P / (Ns * R);
+    const int gl = lane / PR, j = lane - gl * PR, k = j % Ns;
+    const int o = (j / Ns) * Ns * R + k;
+#pragma unroll 1
+    for (int g0 = 0; g0 < GG; g0 += SPR) {
+        if (g0 >= count) break;                    // warp-uniform
+        const int g = g0 + gl;
+        const bool on = gl < SPR && g < count;
+        C v[R];
+        if (on) {
+            const C* b = base + g * gstride;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (Ns == 1) v[r] = j + r * PR < nin ? b[j + r * PR] : cmk<C>(0, 0);
+                else v[r] = b[j + r * PR];
+            }
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = tw[r * k * tstep];
+                    if (!FWD) w = cconj(w);
+                    v[r] = cmul(v[r], w);
+                }
+            }
+            Dft<C, R, FWD>::run(v);
+        }
+        __syncwarp();
+        if (on) {
+            C* b = base + g * gstride + o;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (!LAST || o + r * Ns < nout) b[r * Ns] = v[r];
+        }
+        __syncwarp();
+    }
+}
+
+template <typename C, int P, int GG, int Ns, bool FWD, int... Rs> struct CStages;
+template <typename C, int P, int GG, int Ns, bool FWD> struct CStages<C, P, GG, Ns, FWD> {
+    __device__ __forceinline__ static void run(C*, int, int, const C*, int, int, int) {}
+};
+template <typename C, int P, int GG, int Ns, bool FWD, int R, int... Rest>
+struct CStages<C, P, GG, Ns, FWD, R, Rest...> {
+    __device__ __forceinline__ static void run(C* base, int gstride, int count, const C* tw, int lane, int nin,
+                                               int nout) {
+        cstage<C, P, GG, Ns, R, FWD, sizeof...(Rest) == 0>(base, gstride, count, tw, lane, nin, nout);
+        CStages<C, P, GG, Ns * R, FWD, Rest...>::run(base, gstride, count, tw, lane, nin, nout);
+    }
+};
+
 template <typename C, int P, int G, int Ns, bool FWD, int... Rs> struct GStages;
 template <typename C, int P, int G, int Ns, bool FWD> struct GStages<C, P, G, Ns, FWD> {
     __device__ __forceinline__ static void run(C*, int, const C*, int, int, int) {}
@@ -175,10 +239,15 @@ template <int P> struct Fused { static constexpr bool ok = false; };
 #define TOMO_FUSED(P_, ...)                                                                   \
     template <> struct Fused<P_> {                                                            \
         static constexpr bool ok = true;                                                      \
-        template <typename C, bool FWD>                                                       \
+        template <typename C, bool FWD, int GG>                                               \
         __device__ __forceinline__ static void run(C* base, int gstride, const C* tw, int lane, int nin, \
                                                    int nout) {                                \
-            GStages<C, P_, kFftGroup, 1, FWD, __VA_ARGS__>::run(base, gstride, tw, lane, nin, nout); \
+            GStages<C, P_, GG, 1, FWD, __VA_ARGS__>::run(base, gstride, tw, lane, nin, nout);   \
+        }                                                                                     \
+        template <typename C, bool FWD, int GG>                                               \
+        __device__ __forceinline__ static void run_rounds(C* base, int gstride, int count, const C* tw, int lane, \
+                                                          int nin, int nout) {                \
+            CStages<C, P_, GG, 1, FWD, __VA_ARGS__>::run(base, gstride, count, tw, lane, nin, nout); \
         }                                                                                     \
     };
 #ifndef TOMO_PLAN_150_ID
@@ -220,19 +289,34 @@ TOMO_FUSED(32, 4, 8)
 // Host side: true if P has a fused plan (then the generic scratch is unused).
 inline bool has_fused_plan(int P) { return P == 150 || P == 180 || P == 160 || P == 40 || P == 32; }
 
-// Transforms kFftGroup sequences base[g * gstride + 0..P) in place with one
-// warp; PC is the compile-time size (0: generic, through scratch[0..P)).  Only
-// the first nin inputs may be non-zero (the others are not read) and only the
+// Transforms GG sequences base[g * gstride + 0..P) in place with one warp
+// (the fused plans transform all GG; the generic path only the first count);
+// PC is the compile-time size (0: generic, through scratch[0..P)).  Only the
+// first nin inputs may be non-zero (the others are not read) and only the
 // first nout outputs are needed (the others may be left unwritten) -- the
 // generic path reads and writes everything.  The warp must be converged and
-// the data visible on entry; ends with __syncwarp().
-template <int PC, typename C, bool FWD>
+// the data visible on entry; ends with __syncwarp().  More sequences per call
+// fill more lanes: a stage of radix R runs GG P / R butterflies over 32 lanes.
+template <int PC, typename C, bool FWD, int GG = kFftGroup>
 __device__ __forceinline__ void fft_g(C* base, int gstride, int count, const FftPlan& pl, const C* tw, C* scratch,
                                       int lane, int nin, int nout) {
     if constexpr (Fused<PC>::ok) {
-        Fused<PC>::template run<C, FWD>(base, gstride, tw, lane, nin, nout);
+        Fused<PC>::template run<C, FWD, GG>(base, gstride, tw, lane, nin, nout);
     } else {
-        for (int gi = 0; gi < kFftGroup && gi < count; ++gi)
+        for (int gi = 0; gi < GG && gi < count; ++gi)
+            fft_warp<C>(base + gi * gstride, scratch, pl, tw, FWD, lane, 32);
+    }
+}
+
+// As fft_g, for up to GG sequences (count <= GG of them) in rounds of whole
+// sequences (cstage): any group size at the registers of one round.
+template <int PC, typename C, bool FWD, int GG>
+__device__ __forceinline__ void fft_rounds(C* base, int gstride, int count, const FftPlan& pl, const C* tw,
+                                           C* scratch, int lane, int nin, int nout) {
+    if constexpr (Fused<PC>::ok) {
+        Fused<PC>::template run_rounds<C, FWD, GG>(base, gstride, count, tw, lane, nin, nout);
+    } else {
+        for (int gi = 0; gi < GG && gi < count; ++gi)
             fft_warp<C>(base + gi * gstride, scratch, pl, tw, FWD, lane, 32);
     }
 }

@@ -224,6 +224,12 @@ cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, in
 // thread of the round has read its inputs.
 constexpr int kMaxFramesPerBlock = 8;
 
+// Sequences per warp call of the column transforms (fft_rounds: rounds of
+// whole sequences).  Six fill 30 of 32 lanes in both stages of 150 = 15 x 10
+// (rounds of three sequences at radix 15, of two at radix 10; a group of two
+// leaves 12 lanes idle at radix 15), and a 12-plane frame is two calls.
+constexpr int kColGroup = 6;
+
 template <typename C, int NPI, int NPO>
 __device__ __forceinline__ void block_mul(C* D, int NPmax, int P, int nf, const int* act, const C* __restrict__ Kc) {
     using T = decltype(C::x);
@@ -270,13 +276,21 @@ __device__ __forceinline__ void block_mul(C* D, int NPmax, int P, int nf, const 
 // (one coalesced copy), and thread (ky, p) assembles its row K_p. from it.
 __host__ __device__ constexpr int herm_index(int NP, int p, int q) { return p * NP - p * (p - 1) / 2 + (q - p); }
 
-template <typename C, int NP>
-__device__ __forceinline__ void block_mul_herm(C* D, int NPmax, int P, int nf, const int* act, const C* __restrict__ Kc,
+// am: bit fl set for the active frames of the block.  PS and NPM, when
+// non-zero, are the column length and the plane stride known at compile time
+// (the strides of every shared-memory access then fold into the instruction).
+template <typename C, int NP, int PS, int NPM>
+__device__ __forceinline__ void block_mul_herm(C* D, int NPmax_rt, int P_rt, unsigned am, const C* __restrict__ Kc,
                                                C* Ks) {
     using T = decltype(C::x);
     constexpr int NE = NP * (NP + 1) / 2;
+    const int P = PS ? PS : P_rt;
+    const int NPmax = PS ? NPM : NPmax_rt;
     const int kyr = blockDim.x / NP;
     const int kyl = threadIdx.x / NP, pp = threadIdx.x % NP;
+    // row p of K(ky) from the packed upper triangle: K_pq = Kr[rb + q] for
+    // q >= p, conj(K_qp) = conj(Kr[herm_index(NP, q, 0) + p]) for q < p
+    const int rb = herm_index(NP, pp, 0);
     for (int ky0 = 0; ky0 < P; ky0 += kyr) {
         const int nky = min(kyr, P - ky0);
         {
@@ -300,11 +314,13 @@ __device__ __forceinline__ void block_mul_herm(C* D, int NPmax, int P, int nf, c
             C k[NP];
             const C* Kr = Ks + kyl * NE;
 #pragma unroll
-            for (int q = 0; q < NP; ++q) k[q] = q >= pp ? Kr[herm_index(NP, pp, q)] : cconj(Kr[herm_index(NP, q, pp)]);
+            for (int q = 0; q < NP; ++q)
+                k[q] = q >= pp ? Kr[rb + q] : cconj(Kr[herm_index(NP, q, 0) + pp]);
+            const C* col0 = D + ky;
 #pragma unroll
             for (int fl = 0; fl < kMaxFramesPerBlock; ++fl) {
-                if (fl < nf && act[fl]) {
-                    const C* col = D + (size_t)fl * NPmax * P + ky;
+                if ((am >> fl) & 1u) {
+                    const C* col = col0 + fl * NPmax * P;
                     T ar = 0, ai = 0;
 #pragma unroll
                     for (int q = 0; q < NP; ++q) {
@@ -320,9 +336,10 @@ __device__ __forceinline__ void block_mul_herm(C* D, int NPmax, int P, int nf, c
         }
         __syncthreads();
         if (on) {
+            C* out = D + pp * P + ky;
 #pragma unroll
             for (int fl = 0; fl < kMaxFramesPerBlock; ++fl)
-                if (fl < nf && act[fl]) D[((size_t)fl * NPmax + pp) * P + ky] = y[fl];
+                if ((am >> fl) & 1u) out[fl * NPmax * P] = y[fl];
         }
         __syncthreads();
     }
@@ -368,9 +385,8 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = g.plan.P, n = g.n, m = g.m, nh = g.nh, NPin = g.NPin, NPout = g.NPout;
-    constexpr int G = kFftGroup;
-    int NPmax = NPin > NPout ? NPin : NPout;
-    NPmax += NPmax & 1;                            // even: groups of two planes never cross frames
+    constexpr int G = kColGroup;
+    const int NPmax = NPin > NPout ? NPin : NPout;
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* scr = tw + P;
     C* D = scr + (Fused<PC>::ok ? 0 : kWarps * P); // [Bc][NPmax][P]
@@ -383,6 +399,8 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) act[i] = st ? st[f0 + i].active : 1;
     __syncthreads();
+    unsigned am = 0;                               // active frames of the block, one bit each
+    for (int i = 0; i < nf; ++i) am |= (act[i] ? 1u : 0u) << i;
     // load the columns, one warp per (frame, plane); rows >= n are the zero
     // padding, which the pruned forward transform never reads.  All loads of a
     // warp's two columns are issued before the first store (latency hiding).
@@ -425,18 +443,14 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
             for (int r = 128 + lane; r < n; r += 32) dst[r] = src[r];
         }
     }
-    // an odd plane count leaves a pad plane in the last group: give it zeros
-    if (NPin & 1)
-        for (int i = threadIdx.x; i < nf * P; i += blockDim.x)
-            D[((size_t)(i / P) * NPmax + NPin) * P + i % P] = cmk<C>(0, 0);
     __syncthreads();
     {
-        const int gpf = (NPin + G - 1) / G;        // the last group may include the pad plane
+        const int gpf = (NPin + G - 1) / G;        // the last group of a frame may be partial
         for (int t = warp; t < nf * gpf; t += kWarps) {
             const int fl = t / gpf, q0 = (t % gpf) * G;
             if (!act[fl]) continue;
             C* base = D + ((size_t)fl * NPmax + q0) * P;
-            fft_g<PC, C, true>(base, P, NPin - q0, g.plan, tw, scr + warp * P, lane, n, P);
+            fft_rounds<PC, C, true, G>(base, P, min(G, NPin - q0), g.plan, tw, scr + warp * P, lane, n, P);
         }
     }
     __syncthreads();
@@ -444,28 +458,30 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     const C* Kc = K + (size_t)kx * NPin * P * NPout;
     const C* Kh = K + (size_t)kx * P * (NPin * (NPin + 1) / 2);
     if (herm) {
+#define TOMO_BMH(NP_) block_mul_herm<C, NP_, PC, NP_>(D, NPmax, P, am, Kh, Ks)
         switch (NPin) {
-            case 2: block_mul_herm<C, 2>(D, NPmax, P, nf, act, Kh, Ks); break;
-            case 4: block_mul_herm<C, 4>(D, NPmax, P, nf, act, Kh, Ks); break;
-            case 6: block_mul_herm<C, 6>(D, NPmax, P, nf, act, Kh, Ks); break;
-            case 8: block_mul_herm<C, 8>(D, NPmax, P, nf, act, Kh, Ks); break;
-            case 10: block_mul_herm<C, 10>(D, NPmax, P, nf, act, Kh, Ks); break;
-            case 12: block_mul_herm<C, 12>(D, NPmax, P, nf, act, Kh, Ks); break;
-            case 14: block_mul_herm<C, 14>(D, NPmax, P, nf, act, Kh, Ks); break;
-            default: block_mul_herm<C, 16>(D, NPmax, P, nf, act, Kh, Ks); break;
+            case 2: TOMO_BMH(2); break;
+            case 4: TOMO_BMH(4); break;
+            case 6: TOMO_BMH(6); break;
+            case 8: TOMO_BMH(8); break;
+            case 10: TOMO_BMH(10); break;
+            case 12: TOMO_BMH(12); break;
+            case 14: TOMO_BMH(14); break;
+            default: TOMO_BMH(16); break;
         }
+#undef TOMO_BMH
     } else if (NPin == 12 && NPout == 12) block_mul<C, 12, 12>(D, NPmax, P, nf, act, Kc);
     else if (NPin == 6 && NPout == 6) block_mul<C, 6, 6>(D, NPmax, P, nf, act, Kc);
     else if (NPin == 4 && NPout == 4) block_mul<C, 4, 4>(D, NPmax, P, nf, act, Kc);
     else if (NPin == 2 && NPout == 2) block_mul<C, 2, 2>(D, NPmax, P, nf, act, Kc);
     else block_mul_rt<C>(D, NPmax, P, nf, act, Kc, NPin, NPout);
     {
-        const int gpf = (NPout + G - 1) / G;       // the last group may include the pad plane
+        const int gpf = (NPout + G - 1) / G;       // the last group of a frame may be partial
         for (int t = warp; t < nf * gpf; t += kWarps) {
             const int fl = t / gpf, p0 = (t % gpf) * G;
             if (!act[fl]) continue;
             C* base = D + ((size_t)fl * NPmax + p0) * P;
-            fft_g<PC, C, false>(base, P, NPout - p0, g.plan, tw, scr + warp * P, lane, P, m);
+            fft_rounds<PC, C, false, G>(base, P, min(G, NPout - p0), g.plan, tw, scr + warp * P, lane, P, m);
         }
     }
     __syncthreads();
@@ -483,8 +499,7 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
                      cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw, bool herm) {
     using C = cplx_t<T>;
     if (g.NPin > 16) return cudaErrorInvalidValue;
-    int NPmax = g.NPin > g.NPout ? g.NPin : g.NPout;
-    NPmax += NPmax & 1;
+    const int NPmax = g.NPin > g.NPout ? g.NPin : g.NPout;
     if (herm && (g.NPin != g.NPout || (g.NPin & 1) || g.NPin < 2 || g.NPin > 16)) return cudaErrorInvalidValue;
     const size_t ks = herm ? sizeof(C) * (size_t)(kThreads / g.NPin) * (g.NPin * (g.NPin + 1) / 2) : 0;
     const size_t fixed = sizeof(C) * (size_t)g.plan.P * (1 + (has_fused_plan(g.plan.P) ? 0 : kWarps)) + ks;
@@ -777,24 +792,44 @@ cudaError_t cg_init_scalars(const Launch& L, int B, int nparts, const double* pa
     return cudaGetLastError();
 }
 
-// One thread per frame.  rr_part holds r^T r of the residual that the row-forward
-// pass of this iteration produced (r_k), dot_part the sums p^T Ap, r^T Ap,
-// Ap^T Ap of this iteration's product.  Stops the frame when r_k is small
-// enough (x_k is then final); otherwise alpha_k = r_k^T r_k / p^T Ap and
+// The per-iteration scalar kernels run one warp per frame: lane i loads the
+// partial sums i, i + 32, ... (all loads in flight at once; a serial loop over
+// them was bound by one L2 round trip per partial) and an xor butterfly
+// combines the lanes.  Floating-point addition is commutative, so every lane
+// ends with bitwise the same totals; lane 0 then updates the frame's state.
+constexpr int kScalarWarps = 4;
+
+__device__ __forceinline__ double warp_total(double v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    return v;
+}
+
+// rr_part holds r^T r of the residual that the row-forward pass of this
+// iteration produced (r_k), dot_part the sums p^T Ap, r^T Ap, Ap^T Ap of this
+// iteration's product.  Stops the frame when r_k is small enough (x_k is then
+// final); otherwise alpha_k = r_k^T r_k / p^T Ap and
 // beta_{k+1} = r_{k+1}^T r_{k+1} / r_k^T r_k with the recurrence value
 // r_{k+1}^T r_{k+1} = r_k^T r_k - 2 alpha r_k^T Ap + alpha^2 Ap^T Ap.
-__global__ void k_cg_scalars(int B, int NP, const double* __restrict__ rr_part, const double* __restrict__ dot_part,
-                             FrameState* st) {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= B || !st[f].active) return;
+__global__ void __launch_bounds__(kScalarWarps * 32)
+k_cg_scalars(int B, int NP, const double* __restrict__ rr_part, const double* __restrict__ dot_part,
+             FrameState* st) {
+    const int f = blockIdx.x * kScalarWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (f >= B) return;
+    const int active = st[f].active;
     double rr = 0.0, pAp = 0.0, rAp = 0.0, ApAp = 0.0;
-    for (int i = 0; i < NP; ++i) {
+    for (int i = lane; i < NP; i += 32) {
         rr += rr_part[(size_t)f * NP + i];
         const double* d = dot_part + ((size_t)f * NP + i) * 3;
         pAp += d[0];
         rAp += d[1];
         ApAp += d[2];
     }
+    rr = warp_total(rr);
+    pAp = warp_total(pAp);
+    rAp = warp_total(rAp);
+    ApAp = warp_total(ApAp);
+    if (!active || lane != 0) return;
     FrameState s = st[f];
     s.rr = rr;
     s.relres = sqrt(rr / s.snorm2);
@@ -820,21 +855,28 @@ __global__ void k_cg_scalars(int B, int NP, const double* __restrict__ rr_part, 
 }
 
 cudaError_t cg_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_part, FrameState* st) {
-    k_cg_scalars<<<(B + 127) / 128, 128, 0, L.stream>>>(B, NP, rr_part, dot_part, st);
+    k_cg_scalars<<<(B + kScalarWarps - 1) / kScalarWarps, kScalarWarps * 32, 0, L.stream>>>(B, NP, rr_part, dot_part,
+                                                                                           st);
     count(L);
     return cudaGetLastError();
 }
 
-__global__ void k_pcg_scalars(int B, int NP, const double* __restrict__ rr_part, const double* __restrict__ dot_M,
-                              const double* __restrict__ dot_A, FrameState* st) {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= B || !st[f].active) return;
+__global__ void __launch_bounds__(kScalarWarps * 32)
+k_pcg_scalars(int B, int NP, const double* __restrict__ rr_part, const double* __restrict__ dot_M,
+              const double* __restrict__ dot_A, FrameState* st) {
+    const int f = blockIdx.x * kScalarWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (f >= B) return;
+    const int active = st[f].active;
     double rr = 0.0, gamma = 0.0, delta = 0.0;
-    for (int i = 0; i < NP; ++i) {
+    for (int i = lane; i < NP; i += 32) {
         rr += rr_part[(size_t)f * NP + i];
         gamma += dot_M[((size_t)f * NP + i) * 3];
         delta += dot_A[((size_t)f * NP + i) * 3];
     }
+    rr = warp_total(rr);
+    gamma = warp_total(gamma);
+    delta = warp_total(delta);
+    if (!active || lane != 0) return;
     FrameState s = st[f];
     s.rr = rr;
     s.relres = sqrt(rr / s.snorm2);
@@ -865,29 +907,37 @@ __global__ void k_pcg_scalars(int B, int NP, const double* __restrict__ rr_part,
 
 cudaError_t pcg_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_M,
                         const double* dot_A, FrameState* st) {
-    k_pcg_scalars<<<(B + 127) / 128, 128, 0, L.stream>>>(B, NP, rr_part, dot_M, dot_A, st);
+    k_pcg_scalars<<<(B + kScalarWarps - 1) / kScalarWarps, kScalarWarps * 32, 0, L.stream>>>(B, NP, rr_part, dot_M,
+                                                                                            dot_A, st);
     count(L);
     return cudaGetLastError();
 }
 
-// One thread per frame.  rr_part: r^T r of the residual the row-forward pass
-// produced (r_{k+1}); dot_part: r^T w, Ap^T w, w^T w with w = A r_{k+1} and
-// Ap the direction's product used in that update.  Conjugate residuals:
+// rr_part: r^T r of the residual the row-forward pass produced (r_{k+1});
+// dot_part: r^T w, Ap^T w, w^T w with w = A r_{k+1} and Ap the direction's
+// product used in that update.  Conjugate residuals:
 // p_{k+1} = r_{k+1} + beta p_k, A p_{k+1} = w + beta A p_k, alpha = r^T A r / |A p|^2;
 // for symmetric positive (semi)definite A these are the MINRES iterates
 // (each x_k minimises the residual norm over the Krylov space).
-__global__ void k_mr_scalars(int B, int NP, const double* __restrict__ rr_part, const double* __restrict__ dot_part,
-                             FrameState* st) {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= B || !st[f].active) return;
+__global__ void __launch_bounds__(kScalarWarps * 32)
+k_mr_scalars(int B, int NP, const double* __restrict__ rr_part, const double* __restrict__ dot_part,
+             FrameState* st) {
+    const int f = blockIdx.x * kScalarWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (f >= B) return;
+    const int active = st[f].active;
     double rr = 0.0, rho = 0.0, apw = 0.0, ww = 0.0;
-    for (int i = 0; i < NP; ++i) {
+    for (int i = lane; i < NP; i += 32) {
         rr += rr_part[(size_t)f * NP + i];
         const double* d = dot_part + ((size_t)f * NP + i) * 3;
         rho += d[0];
         apw += d[1];
         ww += d[2];
     }
+    rr = warp_total(rr);
+    rho = warp_total(rho);
+    apw = warp_total(apw);
+    ww = warp_total(ww);
+    if (!active || lane != 0) return;
     FrameState s = st[f];
     s.rr = rr;
     s.relres = sqrt(rr / s.snorm2);
@@ -918,7 +968,8 @@ __global__ void k_mr_scalars(int B, int NP, const double* __restrict__ rr_part, 
 }
 
 cudaError_t mr_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_part, FrameState* st) {
-    k_mr_scalars<<<(B + 127) / 128, 128, 0, L.stream>>>(B, NP, rr_part, dot_part, st);
+    k_mr_scalars<<<(B + kScalarWarps - 1) / kScalarWarps, kScalarWarps * 32, 0, L.stream>>>(B, NP, rr_part, dot_part,
+                                                                                           st);
     count(L);
     return cudaGetLastError();
 }
