@@ -31,6 +31,14 @@ inline void count(const Launch& L) {
 
 static_assert(kRowPairsPerBlock == kWarps * kFftGroup, "a row group is one round of the block's warps");
 
+// Sequences per warp call of fft_rounds (rounds of whole sequences).  Six fill
+// 30 of 32 lanes in both stages of 150 = 15 x 10 (rounds of three sequences at
+// radix 15, of two at radix 10; a call of two leaves 12 lanes idle at radix
+// 15).  The column pass uses it throughout; the row passes use it when one
+// block holds a whole plane (37 row pairs: 7 calls on 8 warps, five round
+// trips each, instead of up to three calls of two round trips), in FP32.
+constexpr int kRoundGroup = 6;
+
 int g_max_smem = 48 * 1024;   // raised by init_kernel_attributes()
 
 template <typename T>
@@ -166,8 +174,17 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
         }
     }
     __syncthreads();
-    for (int gi = warp; gi < ngrp; gi += kWarps)
-        fft_g<PC, C, true>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane, n, P);
+    bool rounds = false;
+    if constexpr (sizeof(T) == 4) {                 // FP64 would spill
+        rounds = gridDim.z == 1;
+        if (rounds)
+            for (int g0 = warp * kRoundGroup; g0 < npl; g0 += kWarps * kRoundGroup)
+                fft_rounds<PC, C, true, kRoundGroup>(F + g0 * RS, RS, min(kRoundGroup, npl - g0), g.plan, tw,
+                                                     scr + warp * P, lane, n, P);
+    }
+    if (!rounds)
+        for (int gi = warp; gi < ngrp; gi += kWarps)
+            fft_g<PC, C, true>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane, n, P);
     if (cgm) {
         const double t = block_sum<T>(rr, red);
         if (threadIdx.x == 0) cg.rr_part[((size_t)f * g.NPin + q) * gridDim.z + blockIdx.z] = t;
@@ -224,11 +241,8 @@ cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, in
 // thread of the round has read its inputs.
 constexpr int kMaxFramesPerBlock = 8;
 
-// Sequences per warp call of the column transforms (fft_rounds: rounds of
-// whole sequences).  Six fill 30 of 32 lanes in both stages of 150 = 15 x 10
-// (rounds of three sequences at radix 15, of two at radix 10; a group of two
-// leaves 12 lanes idle at radix 15), and a 12-plane frame is two calls.
-constexpr int kColGroup = 6;
+// Sequences per warp call of the column transforms: a 12-plane frame is two calls.
+constexpr int kColGroup = kRoundGroup;
 
 template <typename C, int NPI, int NPO>
 __device__ __forceinline__ void block_mul(C* D, int NPmax, int P, int nf, const int* act, const C* __restrict__ Kc) {
@@ -612,8 +626,17 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
         for (int i = threadIdx.x; i < (ngrp * G - npair) * RS; i += blockDim.x) F[npair * RS + i] = cmk<C>(0, 0);
     load_row_pairs<C>(Y1T + ((size_t)f * g.NPout + pp) * nh * m, m, P, nh, RS, F, pb, npair);
     __syncthreads();
-    for (int gi = warp; gi < ngrp; gi += kWarps)
-        fft_g<PC, C, false>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane, P, m);
+    bool rounds = false;
+    if constexpr (sizeof(T) == 4) {                 // FP64 would spill
+        rounds = gridDim.z == 1;
+        if (rounds)
+            for (int g0 = warp * kRoundGroup; g0 < npair; g0 += kWarps * kRoundGroup)
+                fft_rounds<PC, C, false, kRoundGroup>(F + g0 * RS, RS, min(kRoundGroup, npair - g0), g.plan, tw,
+                                                      scr + warp * P, lane, P, m);
+    }
+    if (!rounds)
+        for (int gi = warp; gi < ngrp; gi += kWarps)
+            fft_g<PC, C, false>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane, P, m);
     __syncthreads();
     // gather the valid outputs (W_s), add the noise term, CG dot products
     const size_t vbase = ((size_t)f * g.NPout + pp) * mt.n_vs;
