@@ -65,3 +65,33 @@ def test_missing_library_fails_loudly(tmp_path):
             tomo.lib(str(tmp_path / "nope.so"))
     finally:
         tomo._lib = saved
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # the ctypes mirrors must have the C layout field by field: a C program
+    # built from the header prints every offset and size, compared here
+    import shutil
+    import subprocess
+
+    from paper_1806_07938_gb300 import tomo
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {name: getattr(tomo, name) for name in
+               ("tomo_gs", "tomo_config", "tomo_layout_info", "tomo_solve_opts", "tomo_frame_info")}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tomo.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)

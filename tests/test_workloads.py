@@ -32,3 +32,37 @@ def test_sequence_frozen_flow_moves_the_screens():
     assert d_large > 2 * d_small          # 50 ms of wind decorrelates far more than 1 ms
     c, _ = W.slope_sequence(cfg, 1, 2, seed=4, dt=1e-3)
     assert np.array_equal(a, c)           # deterministic
+
+
+def test_elongated_noise_model():
+    # side-launch elongation (Sec. 2.F): sigma^2 (I + (k/D)^2 v v^T), v from the
+    # launch point at 0.55 D on the star's azimuth to the subaperture centre
+    from paper_1806_07938_gb300 import workloads as W
+    cfg = W.config("lgs_mid")
+    C = W.elongated_noise(cfg, 0.2, k=2.0)
+    n, D = cfg["n"], cfg["D"]
+    assert C.shape == (len(cfg["gs"]), n, n, 3)
+    sxx, syy, sxy = C[..., 0], C[..., 1], C[..., 2]
+    det = sxx * syy - sxy ** 2
+    tr = sxx + syy
+    # eigenvalues: sigma^2 and sigma^2 (1 + (k |v| / D)^2)
+    lo = tr / 2 - np.sqrt((tr / 2) ** 2 - det)
+    assert np.allclose(lo, 0.04, rtol=0, atol=1e-12)
+    # the long axis points at the launch telescope of each laser star
+    for g, (ax, ay, H) in enumerate(cfg["gs"]):
+        th = np.arctan2(ay, ax)
+        lx, ly = 0.55 * D * np.cos(th), 0.55 * D * np.sin(th)
+        c = (np.arange(n) + 0.5) * D / n - D / 2
+        vx = c[None, :] - lx
+        vy = c[:, None] - ly
+        hi = tr[g] - lo[g]
+        assert np.allclose(hi, 0.04 * (1 + (2.0 / D) ** 2 * (vx ** 2 + vy ** 2)), rtol=1e-12)
+        # (vx, vy) is the eigenvector of the larger eigenvalue
+        res_x = (sxx[g] - hi) * vx + sxy[g] * vy
+        res_y = sxy[g] * vx + (syy[g] - hi) * vy
+        assert np.abs(res_x).max() < 1e-12 and np.abs(res_y).max() < 1e-12
+    # natural stars are not elongated
+    ngs = W.config("ngs8m")
+    Cn = W.elongated_noise(ngs, 0.1, k=3.0)
+    assert np.array_equal(Cn[..., 0], np.full(Cn.shape[:3], 0.1 ** 2))
+    assert np.array_equal(Cn[..., 2], np.zeros(Cn.shape[:3]))
