@@ -1,11 +1,14 @@
-// Radix-fused, in-place FFTs of G sequences per warp (included by kernels.cu only).
+// Radix-fused, in-place FFTs of several sequences per warp (included by
+// kernels.cu only).
 //
-// A length-P transform is factored into few composite radices (150 = 10 x 15,
+// A length-P transform is factored into few composite radices (150 = 15 x 10,
 // 180 = 12 x 15, 160 = 10 x 16, 40 = 8 x 5, 32 = 4 x 8).  Each Stockham stage
-// (same ordering as fft.cuh) reads all inputs of all G sequences into
-// registers, synchronises the warp, and writes the outputs back in place, so a
-// 150-point transform costs two shared-memory round trips instead of four and
-// needs no scratch buffer.  A composite radix R = R1 R2 is itself evaluated in
+// (same ordering as fft.cuh) reads its inputs into registers, synchronises the
+// warp, and writes the outputs back in place, so a 150-point transform costs
+// two shared-memory round trips instead of four and needs no scratch buffer.
+// gstage does this for G sequences at once; cstage in rounds of whole
+// sequences, which lets one call take more sequences than the lanes of one
+// round hold.  A composite radix R = R1 R2 is itself evaluated in
 // registers as two small DFTs with the inner twiddles w_R^{b s} (the same
 // two-factor decomposition, Cooley & Tukey 1965), read from __constant__
 // tables that init_fft_constants() fills once.

@@ -15,10 +15,11 @@ constexpr int kThreads = 32 * kWarps;
 #define TOMO_MIN_BLOCKS 3                  // resident blocks per SM the FFT kernels are compiled for
 #endif
 
-// Row passes: one block transforms up to kRowPairsPerBlock row pairs of one
-// plane of one frame (one pair per sequence, kFftGroup sequences per warp), so
-// a plane of n rows is split over row_groups(n) blocks.  Partial sums of the
-// row passes are stored per (frame, plane, row group).
+// Row passes: one block transforms the row pairs of one plane of one frame
+// (one pair per sequence), or, for batches too small to fill the GPU, up to
+// kRowPairsPerBlock of them (kFftGroup sequences per warp), so that a plane of
+// n rows is split over row_groups(n) blocks.  Partial sums of the row passes
+// are stored per (frame, plane, row group).
 constexpr int kRowPairsPerBlock = 16;
 __host__ __device__ constexpr int row_groups(int nrows) {
     return ((nrows + 1) / 2 + kRowPairsPerBlock - 1) / kRowPairsPerBlock;
