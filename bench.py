@@ -121,6 +121,27 @@ def fft_flops(L):
     return 5.0 * L * math.log2(L)
 
 
+def paper_opcounts(n, n_gs, n_layer, n_new, a=5.0):
+    """Operation counts per frame of the paper's 1-D 2RBT products (Sec. 2.E, with an
+    N-point FFT costing a N log2 N operations and a sparse MVM its non-zeros) and of
+    the full MVMs they replace:
+      Sigma_ss zeta:         4 N_gs {(2n-1)^2 [2a log2(2n-1) + N_gs] + n^2}, full 4 N_gs^2 n^4;
+      Sigma_phi_s zeta, NGS: 2 N_gs [4n^2 (2a log2 2n + 1) + n^2] + 8 n^2 log2 2n + (n+1)^2,
+                             full 2 N_gs (n+1)^2 n^2 (the backward-FFT term as printed, without a);
+      Sigma_phi_s zeta, LGS: 2 (n'+n-1)^2 [(2 N_gs + N_layer) a log2(n'+n-1) + N_gs N_layer]
+                             + 2 N_gs n^2 + 4 N_layer (n+1)^2, same full MVM."""
+    L = 2 * n - 1
+    ss = 4 * n_gs * (L * L * (2 * a * math.log2(L) + n_gs) + n * n)
+    ps_ngs = (2 * n_gs * (4 * n * n * (2 * a * math.log2(2 * n) + 1) + n * n) + 8 * n * n * math.log2(2 * n)
+              + (n + 1) ** 2)
+    Lp = n_new + n - 1
+    ps_lgs = (2 * Lp * Lp * ((2 * n_gs + n_layer) * a * math.log2(Lp) + n_gs * n_layer) + 2 * n_gs * n * n
+              + 4 * n_layer * (n + 1) ** 2)
+    ps_full = 2 * n_gs * (n + 1) ** 2 * n * n
+    return {"sigma_ss": ss, "sigma_ss_full": 4 * n_gs ** 2 * n ** 4, "sigma_phi_s_ngs": ps_ngs,
+            "sigma_phi_s_lgs": ps_lgs, "sigma_phi_s_full": ps_full}
+
+
 def kernel_model(layout):
     """Algorithmic flops and bytes per frame-iteration for each MVM pass: complex FFTs at 5 L log2 L
     flops, 8 flops per complex multiply-add of the block product, and the vectors, half spectra and
@@ -595,6 +616,12 @@ def run_ours(args):
         kms, kn, frame_iters = tomo.tomo_get_kernel_timing(h)
         tomo.tomo_set_kernel_timing(h, 0)
         model = kernel_model(layout)
+        # the paper's operation counts for this system beside this design's own model
+        cfg_layers = len(cfg["layers"])
+        opcount = {k: float(v) for k, v in paper_opcounts(layout.n, layout.n_gs, cfg_layers, layout.n_new).items()}
+        opcount["this_design_sigma_ss"] = float(sum(model[k]["flops"] for k in ("rows_fwd", "cols_mul", "rows_inv")))
+        opcount["note"] = ("paper: 1-D 2RBT formulation, a = 5 (Sec. 2.E); this design: 2-D real FFTs on a "
+                           f"{layout.P}^2 torus, Hermitian block product, same FFT cost model")
         pk = peaks()
         alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
         balance = alu_peak * 1e12 / (pk["hbm_gbs"] * 1e9)
@@ -640,6 +667,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "frames_per_gpu": F, "N": layout.N, "P": layout.P,
                        "Pcos": layout.Pcos, "n_new": layout.n_new,
                        "fft_P_autotune": {str(int(p)): round(float(t), 4) for p, t in zip(tune_P, tune_ms)},
+                       "opcount_per_product": opcount,
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
