@@ -179,3 +179,38 @@ def test_elongated_rejects_indefinite_blocks(T):
         ok[0, i, j] = (-1.0, -1.0, 5.0)
         h = T.tomo_create(dict(cfg, noise_cov=ok), stream=torch.cuda.current_stream())
         T.tomo_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def row_group_system():
+    from paper_1806_07938_gb300 import workloads as W
+    cfg = small_cfg(n=36, n_gs=2, lgs=True, obstruction=0.2, D=0.5 * 36, layers=((8000.0, 1.0),), noise=0.2)
+    cfg["noise_cov"] = W.elongated_noise(cfg, 0.2, 3.0)
+    return cfg, cov.system_matrix(cfg)
+
+
+@pytest.mark.parametrize("method,modes_on", [("cg", False), ("minres", False), ("cg", True)])
+def test_elongated_with_row_groups(T, row_group_system, method, modes_on):
+    # n = 36 has 18 row pairs: a small batch runs the row passes as two blocks
+    # per plane, whose partial sums the per-WFS passes (noise blocks, then the
+    # mode projection) must rewrite for every row group
+    from oracle import modes
+    cfg, A = row_group_system
+    s = np.random.default_rng(36).standard_normal((2, A.shape[0]))
+    h = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=2, mode_removal=modes_on)
+    try:
+        tol = 1.5e-4                    # cond(A) ~ 4e4: the FP32 floor is near 6e-5 here
+        z, _, info = solve_gpu(T, h, s, tol=tol, max_iter=20000, max_refine=5, method=method)
+        print("row groups", method, modes_on, info)
+        assert (info["status"] == 0).all() and (info["relres"] <= tol).all()
+        if modes_on:
+            zs, _ = modes.reconstruct(cfg, s.T, A)
+            Ms = modes.slope_removal(cfg)
+            bound = info["relres"] * np.linalg.norm(s @ Ms, axis=1) / 0.2 ** 2
+            assert (np.linalg.norm(z - zs.T, axis=1) <= bound).all()
+        else:
+            zs = solve.solve_cholesky(A, s.T).T
+            bound = info["relres"] * np.linalg.norm(s, axis=1) / 0.2 ** 2
+            assert (np.linalg.norm(z - zs, axis=1) <= bound).all()
+    finally:
+        T.tomo_destroy(h)
