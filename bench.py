@@ -142,6 +142,20 @@ def paper_opcounts(n, n_gs, n_layer, n_new, a=5.0):
             "sigma_phi_s_lgs": ps_lgs, "sigma_phi_s_full": ps_full}
 
 
+def whole_product(model, frames, step_ms, iters_mean, hbm_gbs, alu_tflops):
+    """The three passes of one product taken as a unit: algorithmic bytes and flops per
+    frame-iteration (the spectra once per launch of ``frames``), their intensity against
+    the FP32 ridge, the HBM-bound time, and the solve's measured time per
+    frame-iteration (every kernel of the step included) as a fraction of that bound."""
+    byts = sum(m["bytes"] for m in model.values()) + sum(m["per_launch_bytes"] for m in model.values()) / frames
+    flops = sum(m["flops"] for m in model.values())
+    bound_s = byts / (hbm_gbs * 1e9)
+    meas_s = step_ms / 1000.0 / (frames * iters_mean)
+    return {"bytes_per_frame_iter": byts, "flops_per_frame_iter": flops, "flop_per_byte": flops / byts,
+            "ridge_flop_per_byte": alu_tflops * 1e12 / (hbm_gbs * 1e9), "hbm_bound_us": bound_s * 1e6,
+            "solve_us_per_frame_iter": meas_s * 1e6, "frac_of_hbm_bound": bound_s / meas_s}
+
+
 def kernel_model(layout):
     """Algorithmic flops and bytes per frame-iteration for each MVM pass: complex FFTs at 5 L log2 L
     flops, 8 flops per complex multiply-add of the block product, and the vectors, half spectra and
@@ -150,7 +164,7 @@ def kernel_model(layout):
     nh = P // 2 + 1
     rows_fft = NP * math.ceil(n / 2) * fft_flops(P)           # two real rows per complex FFT
     inter = NP * nh * n * 8                                    # one pass of the column-major half spectrum
-    spectra = nh * P * NP * NP * 8                             # complex64 K(f), read once per launch
+    spectra = nh * P * (NP * (NP + 1) // 2) * 8               # Hermitian K(f): the 78 upper blocks, once per launch
     return {
         # CG mode: reads x, r, p, Ap and writes x, r, p (the fused update), writes the half spectrum
         "rows_fwd": dict(flops=rows_fft, bytes=7 * N * 4 + inter, per_launch_bytes=0),
@@ -642,6 +656,8 @@ def run_ours(args):
                                if roof["bound"] == "alu" else f"HBM copy, {pk['src']}")
         roof["avg_launch_us"] = 1000.0 * kms[dom] / max(1, kn[dom])
         roof["kernel_ms"] = {k: round(v, 3) for k, v in kms.items()}
+        roof["whole_product"] = whole_product(model, F, total_ms / args.steps, float(iters.mean()), pk["hbm_gbs"],
+                                              alu_peak)
 
         # end to end through the public host-buffer API, inputs in pinned memory
         s_h = torch.empty((F, layout.N), dtype=torch.float32, pin_memory=True)
