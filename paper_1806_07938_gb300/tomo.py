@@ -140,7 +140,13 @@ def _hptr(a, dtype):
 
 
 def make_config(cfg, max_batch=1, fft_P=0, fft_Pcos=0, precond=False, precond_floor=0.0, mode_removal=False):
-    """tomo_config from the plain-number system description; keeps its arrays alive."""
+    """tomo_config from the plain-number system description; keeps its arrays alive.
+
+    Keys of ``cfg``: D, obstruction, n, r0, L0; gs = [(alpha_x, alpha_y, H)] (H = 0
+    for a natural star); noise_sigma = [sigma per guide star]; layers = [(h, fraction)];
+    targets = [(beta_x, beta_y)]; optional slope_model ("hudgin" or "fried") and
+    noise_cov ([n_gs][n][n][3] = s_xx, s_yy, s_xy per subaperture, elongated laser
+    spots).  Angles in radians, lengths in metres."""
     n_gs = len(cfg["gs"])
     gs = (tomo_gs * n_gs)()
     for g, (ax, ay, H) in enumerate(cfg["gs"]):
