@@ -81,7 +81,7 @@ struct tomo_handle {
     int* d_rowstart = nullptr;
     int* d_col = nullptr;
     int* d_rowcol = nullptr;
-    double* d_noise_var = nullptr;
+    double* d_noise_var = nullptr;     // sigma_g^2 per plane: the diagonal noise, the preconditioner's floor
     float2* d_tw32 = nullptr;
     double2* d_tw64 = nullptr;
     float2* d_twc32 = nullptr;
