@@ -84,3 +84,35 @@ def test_noise_weighted_reconstructor_is_optimal():
     R_white = solve.reconstructor(F, cov.system_matrix(dict(cfg, noise_cov=None)))
     mismatched = wfe.analytic_wfe(cfg, 0, R=R_white)
     assert mismatched > best * (1 + 1e-3)
+
+
+def test_analytic_wfe_noise_term_matches_sampled_noise():
+    # Eq. analytical1 with the turbulence switched off (r0 -> 1e9: every
+    # covariance scales as r0^{-5/3}) keeps only the noise term of a fixed R:
+    # mean square of P R eta over eta drawn from each subaperture's 2 x 2 block
+    from oracle import solve, wfe
+    cfg = elongated(n=6, k=4.0)
+    R = solve.reconstructor(cov.cos_interp(cfg, 0), cov.system_matrix(cfg))
+    quiet = dict(cfg, r0=1e9)
+    ana = wfe.analytic_wfe(quiet, 0, R=R)
+    mask = geo.subaperture_mask(cfg["n"], cfg["obstruction"])
+    C = cfg["noise_cov"]
+    l11 = np.sqrt(C[..., 0])
+    l21 = C[..., 2] / l11
+    l22 = np.sqrt(C[..., 1] - l21 ** 2)
+    rng = np.random.default_rng(77)
+    vals = []
+    for _ in range(10):
+        u = rng.standard_normal((4000, 2) + C.shape[:3])
+        eta = np.stack([l11 * u[:, 0], l21 * u[:, 0] + l22 * u[:, 1]], axis=2)[..., mask].reshape(4000, -1)
+        e = eta @ R.T
+        e = e - e.mean(axis=1, keepdims=True)
+        vals.append(np.mean(e * e, axis=1))
+    vals = np.concatenate(vals)
+    mc, se = vals.mean(), vals.std() / np.sqrt(len(vals))
+    assert abs(mc - ana) <= 4 * se
+    # dropping the x/y coupling of the blocks moves the term by many errors
+    flat = cfg["noise_cov"].copy()
+    flat[..., 2] = 0.0
+    ana_flat = wfe.analytic_wfe(dict(quiet, noise_cov=flat), 0, R=R)
+    assert abs(ana_flat - ana) > 10 * se
