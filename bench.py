@@ -145,15 +145,18 @@ def paper_opcounts(n, n_gs, n_layer, n_new, a=5.0):
 def whole_product(model, frames, step_ms, iters_mean, hbm_gbs, alu_tflops):
     """The three passes of one product taken as a unit: algorithmic bytes and flops per
     frame-iteration (the spectra once per launch of ``frames``), their intensity against
-    the FP32 ridge, the HBM-bound time, and the solve's measured time per
-    frame-iteration (every kernel of the step included) as a fraction of that bound."""
+    the FP32 ridge, the HBM-bound and FP32-bound times, and the solve's measured time per
+    frame-iteration (every kernel of the step included) as a fraction of the HBM bound
+    and of the larger of the two bounds."""
     byts = sum(m["bytes"] for m in model.values()) + sum(m["per_launch_bytes"] for m in model.values()) / frames
     flops = sum(m["flops"] for m in model.values())
     bound_s = byts / (hbm_gbs * 1e9)
+    alu_s = flops / (alu_tflops * 1e12)
     meas_s = step_ms / 1000.0 / (frames * iters_mean)
     return {"bytes_per_frame_iter": byts, "flops_per_frame_iter": flops, "flop_per_byte": flops / byts,
             "ridge_flop_per_byte": alu_tflops * 1e12 / (hbm_gbs * 1e9), "hbm_bound_us": bound_s * 1e6,
-            "solve_us_per_frame_iter": meas_s * 1e6, "frac_of_hbm_bound": bound_s / meas_s}
+            "alu_bound_us": alu_s * 1e6, "solve_us_per_frame_iter": meas_s * 1e6,
+            "frac_of_hbm_bound": bound_s / meas_s, "frac_of_roofline": max(bound_s, alu_s) / meas_s}
 
 
 def kernel_model(layout):

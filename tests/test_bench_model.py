@@ -39,3 +39,6 @@ def test_whole_product_fraction():
     assert w["flop_per_byte"] < w["ridge_flop_per_byte"]
     assert abs(w["frac_of_hbm_bound"] - 0.177) < 1e-3
     assert abs(w["hbm_bound_us"] / w["solve_us_per_frame_iter"] - w["frac_of_hbm_bound"]) < 1e-12
+    # below the ridge the HBM bound is the larger one
+    assert w["alu_bound_us"] < w["hbm_bound_us"] and w["frac_of_roofline"] == w["frac_of_hbm_bound"]
+    assert abs(w["alu_bound_us"] - 27.836217216e6 / 80.54784e12 * 1e6) < 1e-9
