@@ -109,13 +109,13 @@ typedef struct {
                               the pupil are ignored) the 2 x 2 covariance of its
                               x and y slope noise (elongated laser spots,
                               Sec. 2.F).  It replaces noise_sigma in
-                              Sigma_eta_eta; noise_sigma still sets the
-                              preconditioner's floor, and the mean of
-                              (s_xx + s_yy) / 2 over a guide star's valid
-                              subapertures is a good value for its
-                              noise_sigma^2 (PCG needs 17-28 % fewer
-                              iterations than with the smaller eigenvalue on
-                              the 16 x 16 system).  Each valid block must be
+                              Sigma_eta_eta, and the preconditioner's floor
+                              for a guide star becomes the mean of
+                              (s_xx + s_yy) / 2 over its valid subapertures
+                              (PCG needs 17-28 % fewer iterations than with
+                              the blocks' smaller eigenvalue on the 16 x 16
+                              system); noise_sigma is then not used.  Each
+                              valid block must be
                               positive semidefinite (TOMO_EINVAL otherwise).
                               Read during tomo_create only. */
 } tomo_config;

@@ -675,6 +675,17 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
                 }
         TRY(dalloc(h, &h->d_ncov, nc));
         TRY(upload(h, blocks.data(), h->d_ncov, sizeof(double) * nc));
+        // the preconditioner's noise floor of each guide star: the mean
+        // eigenvalue (s_xx + s_yy) / 2 of its blocks
+        if (h->n_vs > 0) {
+            for (int g = 0; g < h->n_gs; ++g) {
+                double t = 0.0;
+                for (int e = 0; e < h->n_vs; ++e)
+                    t += 0.5 * (blocks[((size_t)g * h->n_vs + e) * 3] + blocks[((size_t)g * h->n_vs + e) * 3 + 1]);
+                nvar[2 * g] = nvar[2 * g + 1] = t / h->n_vs;
+            }
+            TRY(upload(h, nvar.data(), h->d_noise_var, sizeof(double) * h->NP));
+        }
         const std::vector<double> zero(h->NP, 0.0);
         TRY(dalloc(h, &h->d_rows_noise, h->NP));
         TRY(upload(h, zero.data(), h->d_rows_noise, sizeof(double) * h->NP));
