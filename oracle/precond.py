@@ -46,6 +46,18 @@ def periodised_generators(cfg, P):
     return t
 
 
+def noise_floor(cfg):
+    """sigma_g^2 of each guide star for the preconditioner: noise_sigma^2, or with
+    elongated-spot blocks (cfg["noise_cov"]) the mean of (s_xx + s_yy) / 2 over
+    the guide star's valid subapertures, the blocks' mean eigenvalue."""
+    C = cfg.get("noise_cov")
+    if C is None:
+        return np.asarray(cfg["noise_sigma"], np.float64) ** 2
+    mask = geo.subaperture_mask(cfg["n"], cfg["obstruction"])
+    C = np.asarray(C, np.float64)
+    return np.array([0.5 * (C[g][mask][:, 0] + C[g][mask][:, 1]).mean() for g in range(len(cfg["gs"]))])
+
+
 def spectra(cfg, P, floor=3.0):
     """M(f) = (K_+(f) + floor diag(sigma^2))^{-1} as [ky][kx][p][q] (rfft2 half spectrum)."""
     t = periodised_generators(cfg, P)
@@ -57,7 +69,7 @@ def spectra(cfg, P, floor=3.0):
     K = np.transpose(K, (2, 3, 0, 1))
     K = 0.5 * (K + np.conj(np.swapaxes(K, 2, 3)))
     ev, V = np.linalg.eigh(K)
-    sig2 = np.repeat(np.asarray(cfg["noise_sigma"], np.float64) ** 2, 2)
+    sig2 = np.repeat(noise_floor(cfg), 2)
     Kp = np.einsum("yxpk,yxk,yxqk->yxpq", V, np.maximum(ev, 0.0), V.conj()) + floor * np.diag(sig2)
     return np.linalg.inv(Kp)
 

@@ -116,3 +116,19 @@ def test_analytic_wfe_noise_term_matches_sampled_noise():
     flat[..., 2] = 0.0
     ana_flat = wfe.analytic_wfe(dict(quiet, noise_cov=flat), 0, R=R)
     assert abs(ana_flat - ana) > 10 * se
+
+
+def test_preconditioner_floor_with_block_noise():
+    # without elongation the floor is noise_sigma^2 and the spectra are those of
+    # the white-noise system; elongation raises each laser star's floor to the
+    # blocks' mean eigenvalue, above sigma^2, and M stays positive definite
+    from oracle import precond
+    base = small_cfg(n=6, lgs=True, obstruction=0.2, D=3.6, noise=0.15)
+    iso = dict(base, noise_cov=W.elongated_noise(base, 0.15, 0.0))
+    assert np.allclose(precond.noise_floor(iso), 0.15 ** 2, rtol=1e-15, atol=0)
+    assert np.array_equal(precond.spectra(iso, 12), precond.spectra(base, 12))
+    el = dict(base, noise_cov=W.elongated_noise(base, 0.15, 3.0))
+    fl = precond.noise_floor(el)
+    assert (fl > 0.15 ** 2).all()
+    M = precond.spectra(el, 12)
+    assert np.linalg.eigvalsh(0.5 * (M + np.conj(np.swapaxes(M, -1, -2)))).min() > 0
