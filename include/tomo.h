@@ -66,8 +66,12 @@ typedef enum {
 /* Per-frame solver outcome (tomo_frame_info.status). */
 enum {
     TOMO_FRAME_CONVERGED = 0,  /* FP64 true relative residual <= tol           */
-    TOMO_FRAME_MAXIT = 1,      /* iteration limit reached first                */
-    TOMO_FRAME_BREAKDOWN = 2   /* p^T A p <= 0 or not finite                   */
+    TOMO_FRAME_MAXIT = 1,      /* iteration limit (or opts.deadline_ms) first  */
+    TOMO_FRAME_BREAKDOWN = 2   /* p^T A p <= 0, or a NaN / infinity in the
+                                  frame's slopes, warm start or iterates: the
+                                  frame stops and returns its last iterate
+                                  (the initial guess when its input is not
+                                  finite); the other frames are not affected */
 };
 
 /* One guide star (Sec. 2 intro): direction alpha [rad] and altitude H [m];
@@ -149,7 +153,33 @@ typedef struct {
     int check_every;       /* iterations between host convergence checks (>= 1)   */
     int precond;           /* 1: preconditioned CG with the block-circulant M     */
     int method;            /* TOMO_METHOD_CG (0), _MINRES (1) or _BLOCK (2)        */
+    int precision;         /* TOMO_PREC_FP32 (0), _FP64 (1) or _MIXED (2), below   */
+    double inner_tol;      /* TOMO_PREC_MIXED: relative residual reduction asked
+                              of each inner FP32 solve; 0 = automatic (the
+                              remaining factor to tol, at least 2e-5)           */
+    double deadline_ms;    /* > 0: wall-clock budget of the call, checked at
+                              every convergence check; when it is spent the
+                              frames still iterating stop (TOMO_FRAME_MAXIT),
+                              the outputs are written as usual and the call
+                              returns TOMO_ETIMEOUT                             */
 } tomo_solve_opts;
+
+/* Arithmetic of a solve (tomo_solve_opts.precision).
+ * TOMO_PREC_FP32: FP32 vectors, FFTs and spectra, FP64 dot products and
+ *   alpha/beta, FP64 true residual at exit with restarts from it (the
+ *   default).  FP32 storage of zeta floors the relative residual near 1e-5.
+ * TOMO_PREC_FP64: everything in FP64 (vectors, FFTs, spectra, scalars);
+ *   tomo_solve_f64 only, method CG without preconditioner.
+ * TOMO_PREC_MIXED: iterative refinement with an FP64 outer loop: zeta is
+ *   accumulated in FP64, each pass computes the FP64 true residual
+ *   r = s - A zeta with the FP64 operator and solves A d = r with the FP32
+ *   machinery of TOMO_PREC_FP32 (any method and preconditioner) to
+ *   inner_tol, then zeta += d in FP64; it reaches FP64-level residuals at
+ *   FP32 speed per iteration.  tomo_frame_info.iters sums the inner
+ *   iterations, refinements counts the outer passes after the first.
+ *   With tomo_solve the FP64 zeta is rounded to FP32 on output (relres is
+ *   that of the FP64 iterate); tomo_solve_f64 returns it in FP64. */
+enum { TOMO_PREC_FP32 = 0, TOMO_PREC_FP64 = 1, TOMO_PREC_MIXED = 2 };
 
 /* Krylov method of tomo_solve (tomo_solve_opts.method).  The paper tests CG
  * and MINRES, both unpreconditioned (Sec. 2.G).  MINRES runs in its
@@ -232,11 +262,13 @@ tomo_status tomo_apply_css(tomo_handle* h, const float* x_dev, float* y_dev, int
  * nothing: the two intermediate half spectra of the product live in a 16 MiB
  * static device buffer of the library, which every GPU that loads the library
  * keeps until the process exits.  Frames are processed in chunks that fit the
- * buffer; TOMO_ERANGE if a single frame does not fit (2 * 2nGS * (P/2+1) * n
- * complex floats must be <= 16 MiB; the 74 x 74, 6-star system needs 1.08 MB).
+ * buffer (at most 65535 frames per chunk); TOMO_ERANGE if a single frame does
+ * not fit (2 * 2nGS * (P/2+1) * n complex floats must be <= 16 MiB; the
+ * 74 x 74, 6-star system needs 1.08 MB, 15 frames per chunk).
  * Same arguments, result and stream as tomo_apply_css.  The first call on a
  * device looks up the buffer's device address, so make it before any stream
- * capture.  All calls share the buffer and leave their intermediates in it
+ * capture; the address is kept until the process exits, so do not call this
+ * on a device after cudaDeviceReset (which also invalidates every handle).  All calls share the buffer and leave their intermediates in it
  * (nothing in it needs to start at zero: each call writes every element it
  * reads); calls that overlap on the GPU, on different streams or handles,
  * race on it. */
@@ -297,8 +329,10 @@ tomo_status tomo_apply_reconstructor(tomo_handle* h, const float* R_dev, int row
  * opts->warm_start); phase_dev [batch][n_targets][n_vphi] or NULL to skip the
  * projection; info_host [batch] host memory or NULL.  opts NULL = defaults
  * (tol 1e-4, max_iter 10000, max_refine 2, cold start, check_every 32, no
- * preconditioner).
- * Synchronises the stream at each convergence check. */
+ * preconditioner, TOMO_PREC_FP32, no deadline).  opts->precision FP32 or
+ * MIXED (FP64 is tomo_solve_f64's).
+ * Synchronises the stream at each convergence check.  TOMO_ETIMEOUT when
+ * opts->deadline_ms ran out (outputs and info are still written). */
 tomo_status tomo_solve(tomo_handle* h, const float* slopes_dev, int batch,
                        const tomo_solve_opts* opts, float* zeta_dev, float* phase_dev,
                        tomo_frame_info* info_host);
@@ -338,6 +372,18 @@ tomo_status tomo_solve_r0(tomo_handle* h, const float* slopes_dev, int batch,
  * ||M_s s - M_s A M_s zeta|| / ||M_s s||, and tomo_apply_css / tomo_apply_cos
  * keep applying the operators without the projections.  The paper applies
  * it to laser guide stars; here it applies to every WFS of the handle. */
+
+/* The solve on FP64 slopes and solution (config of the 8 m system of Sec. 3,
+ * stated in FP64): slopes_dev, zeta_dev [batch][N] device doubles (zeta_dev
+ * holds the initial guess if opts->warm_start = 1; warm_start 2 is EINVAL).
+ * opts->precision TOMO_PREC_FP64 runs textbook CG (Sec. 2.G) entirely in
+ * FP64: the FP64 2RBT product of tomo_apply_css_f64, FP64 vectors, dot
+ * products and alpha/beta (method CG and precond 0 only, EINVAL otherwise);
+ * TOMO_PREC_MIXED the FP64-outer refinement described above (any method);
+ * TOMO_PREC_FP32 is EINVAL here.  No projection (apply tomo_apply_cos to the
+ * rounded zeta).  Synchronises like tomo_solve. */
+tomo_status tomo_solve_f64(tomo_handle* h, const double* slopes_dev, int batch, const tomo_solve_opts* opts,
+                           double* zeta_dev, tomo_frame_info* info_host);
 
 /* tomo_solve on host buffers: copies slopes in and zeta / phase out around the
  * solve (phase_host may be NULL).  Returns after the stream has finished. */

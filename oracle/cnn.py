@@ -11,6 +11,12 @@ Loss: ||zeta_0 - t||^2 / ||t||^2 over the batch.
 Everything is written out with numpy loops over the 9 taps; gradients are the
 plain chain rule.  Pinned by tests/test_oracle_cnn.py (scipy correlate2d,
 central finite differences).
+
+Training uses Adam (Kingma & Ba, "Adam: a method for stochastic
+optimization", ICLR 2015, Algorithm 1); ``adam_step`` is that algorithm's
+update written out in FP64, pinned by tests/test_oracle_cnn.py (closed forms
+for the first step and for a constant gradient, scale invariance, and a
+worked two-step example).
 """
 
 import numpy as np
@@ -139,3 +145,20 @@ def loss_and_grad(params, slopes, target, n, obstruction, hidden, in_scale, out_
         flat.append(dW.ravel())
         flat.append(db)
     return loss, np.concatenate(flat)
+
+
+def adam_step(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) at step t >= 1, FP64.
+
+    First and second moment estimates m <- beta1 m + (1 - beta1) g and
+    v <- beta2 v + (1 - beta2) g^2, their bias-corrected values
+    m / (1 - beta1^t) and v / (1 - beta2^t), and the parameter step
+    w <- w - lr m_hat / (sqrt(v_hat) + eps).  Returns (w, m, v); the inputs
+    are not modified."""
+    w = np.asarray(w, np.float64)
+    g = np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return w - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

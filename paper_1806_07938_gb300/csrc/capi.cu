@@ -14,6 +14,7 @@
 // Noise: Sigma_eta_eta = sigma_g^2 I per guide star (Sec. 2.B), applied as a
 // diagonal term after the masked gather (Eq. SAap1).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -147,6 +148,16 @@ struct tomo_handle {
     long long kt_n[TOMO_NKERNELS] = {0};
     long long frame_iters = 0;   // sum over frames of CG iterations in solves since the last reset
     std::vector<cudaEvent_t> ev;
+    // FP64 solves (tomo_solve_f64) and the FP64 outer loop of mixed precision,
+    // allocated on first use: vectors [B][N], partial sums [B][nparts] (x3 for dots)
+    double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *Ap64 = nullptr, *s64 = nullptr;
+    double *rr64_part = nullptr, *dot64_part = nullptr;
+    double *rel64 = nullptr, *snorm64 = nullptr;     // per frame: outer relative residual, ||s||^2
+    float *rhs32 = nullptr, *d32 = nullptr;          // inner right-hand side and correction
+    double2* d_fs_outer = nullptr;                   // per-frame (c_f, nu_f) of the outer operator
+    // wall-clock budget of the current call (tomo_solve_opts.deadline_ms)
+    bool has_deadline = false, timed_out = false;
+    std::chrono::steady_clock::time_point deadline{};
 };
 
 namespace {
@@ -268,15 +279,50 @@ CgVecs cg_vecs(tomo_handle* h, int mode, double* dots) {
     return CgVecs{h->x, h->r, h->p, h->Ap, h->rr_part, dots, mode, h->z, h->w};
 }
 
+// FP64 product; with st, frames that are not active are skipped (y keeps its values there).
 tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double* y, int B,
-                       const double2* fscale = nullptr) {
+                       const double2* fscale = nullptr, const FrameState* st = nullptr) {
     const int rg = rg_for(h, B);
-    CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, nullptr, h->X1d, h->d_tw64, rg)));
-    CK((cols_mul<double>(L, h->g_ss, B, nullptr, h->X1d, h->Y1d, h->d_K64, h->d_tw64, false)));
-    CK((rows_inv_masked<double, double>(L, h->g_ss, h->mt, B, nullptr, h->Y1d, x, h->d_rows_noise, fscale, y,
+    CK((rows_fwd<double, double>(L, h->g_ss, h->mt, B, x, nullptr, st, h->X1d, h->d_tw64, rg)));
+    CK((cols_mul<double>(L, h->g_ss, B, st, h->X1d, h->Y1d, h->d_K64, h->d_tw64, false)));
+    CK((rows_inv_masked<double, double>(L, h->g_ss, h->mt, B, st, h->Y1d, x, h->d_rows_noise, fscale, y,
                                         nullptr, h->d_tw64, rg)));
     if (h->d_ncov)
-        CK(noise_blocks<double>(L, B, h->n_vs, h->n_gs, rg, h->d_ncov, fscale, nullptr, y, x, nullptr, nullptr));
+        CK(noise_blocks<double>(L, B, h->n_vs, h->n_gs, rg, h->d_ncov, fscale, st, y, x, nullptr, nullptr));
+    return TOMO_OK;
+}
+
+// Wall-clock budget of a solve call (tomo_solve_opts.deadline_ms).
+void begin_call(tomo_handle* h, const tomo_solve_opts& o) {
+    h->timed_out = false;
+    h->has_deadline = o.deadline_ms > 0;
+    if (h->has_deadline)
+        h->deadline = std::chrono::steady_clock::now() +
+                      std::chrono::microseconds((long long)std::ceil(o.deadline_ms * 1000.0));
+}
+
+bool past_deadline(tomo_handle* h) {
+    if (!h->has_deadline || std::chrono::steady_clock::now() < h->deadline) return false;
+    h->timed_out = true;
+    return true;
+}
+
+// Buffers of the FP64 solves and of the mixed-precision outer loop (first use).
+tomo_status ensure_f64(tomo_handle* h) {
+    if (h->x64) return TOMO_OK;
+    const size_t BN = (size_t)h->max_batch * h->N, B = h->max_batch;
+    TRY(dalloc(h, &h->x64, BN));
+    TRY(dalloc(h, &h->r64, BN));
+    TRY(dalloc(h, &h->p64, BN));
+    TRY(dalloc(h, &h->Ap64, BN));
+    TRY(dalloc(h, &h->s64, BN));
+    TRY(dalloc(h, &h->rr64_part, B * h->nparts));
+    TRY(dalloc(h, &h->dot64_part, B * h->nparts * 3));
+    TRY(dalloc(h, &h->rel64, B));
+    TRY(dalloc(h, &h->snorm64, B));
+    TRY(dalloc(h, &h->rhs32, BN));
+    TRY(dalloc(h, &h->d32, BN));
+    TRY(dalloc(h, &h->d_fs_outer, B));
     return TOMO_OK;
 }
 
@@ -306,7 +352,11 @@ tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi
 // One MINRES iteration (conjugate-residual form): the previous update and FFT
 // of r (row-forward), w = A r with r^T w, Ap^T w, w^T w (column and
 // row-inverse passes), and the per-frame scalars.
-enum IterKind { kIterCG = 0, kIterPCG = 1, kIterMINRES = 2 };
+//
+// One FP64 CG iteration (tomo_solve_f64): the scheduled update and new
+// direction (cg64_update), A p with the FP64 product, the partial sums, and
+// the per-frame scalars.
+enum IterKind { kIterCG = 0, kIterPCG = 1, kIterMINRES = 2, kIterCG64 = 3 };
 
 tomo_status iteration(tomo_handle* h, const Launch& L, int B, int kind, std::vector<std::pair<int, int>>* marks) {
     int last = -1;
@@ -324,6 +374,18 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, int kind, std::vec
     // slot encoding: pair (start event * 8 + kernel class, end event)
     const int rg = rg_for(h, B);
     TRY(mark(0));
+    if (kind == kIterCG64) {
+        CK(cg64_update(L, B, h->N, h->nparts, h->st, h->x64, h->r64, h->p64, h->Ap64, h->rr64_part));
+        TRY(mark(0));
+        TRY(apply_ss64(h, L, h->p64, h->Ap64, B, h->d_fscale, h->st));
+        if (h->modes)
+            CK(mode_project<double>(L, B, 2 * h->n_vs, h->n_gs, 1, h->d_Qs, h->st, h->Ap64, nullptr, nullptr));
+        TRY(mark(2));
+        CK(cg64_dots(L, B, h->N, h->nparts, h->st, h->p64, h->r64, h->Ap64, h->dot64_part));
+        CK(cg_scalars(L, B, h->nparts, h->rr64_part, h->dot64_part, h->st));
+        TRY(mark(3));
+        return TOMO_OK;
+    }
     if (kind == kIterMINRES) {
         const CgVecs cg = cg_vecs(h, 3, h->dot_part);
         CK((rows_fwd<float, float>(L, h->g_ss, h->mt, B, nullptr, &cg, h->st, h->X1, h->d_tw32, rg)));
@@ -1093,6 +1155,54 @@ tomo_status set_fscale(tomo_handle* h, int B, const double* c, const double* nu)
     return TOMO_OK;
 }
 
+// The host loop of the single-vector methods: graphs of check_every
+// iterations, with a convergence check between them; when no frame is active
+// the FP64 true residual (true_res) decides which frames restart.  Stops the
+// frames still active when max_iter iterations are spent or the call's
+// deadline has passed (TOMO_FRAME_MAXIT).
+template <typename TrueRes>
+tomo_status run_iterations(tomo_handle* h, const Launch& L, int B, const tomo_solve_opts& o, int kind,
+                           TrueRes&& true_res) {
+    const int chunk = std::max(1, o.check_every);
+    if (!h->timing) TRY(build_graph(h, B, chunk, kind));
+    long long total_iters = 0;
+    std::vector<std::pair<int, int>> marks;
+    for (;;) {
+        CK(count_active(L, B, h->st, h->d_nactive));
+        CK(cudaMemcpyAsync(h->h_nactive, h->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, h->work));
+        CK(cudaStreamSynchronize(h->work));
+        if (h->timing) collect_timing(h, marks);
+        if (*h->h_nactive == 0) {
+            // FP64 true residual s - A zeta and restart of the frames above tol
+            TRY(true_res(o.max_refine));
+            CK(count_active(L, B, h->st, h->d_nactive));
+            CK(cudaMemcpyAsync(h->h_nactive, h->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, h->work));
+            CK(cudaStreamSynchronize(h->work));
+            if (*h->h_nactive == 0) break;
+        }
+        if (total_iters >= (long long)o.max_iter || past_deadline(h)) {
+            // iteration budget or time spent: stop the remaining frames
+            std::vector<FrameState> tmp(B);
+            CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
+            CK(cudaStreamSynchronize(h->work));
+            for (auto& f : tmp)
+                if (f.active) { f.active = 0; f.status = TOMO_FRAME_MAXIT; }
+            CK(cudaMemcpyAsync(h->st, tmp.data(), sizeof(FrameState) * B, cudaMemcpyHostToDevice, h->work));
+            CK(cudaStreamSynchronize(h->work));
+            TRY(true_res(0));
+            break;
+        }
+        if (h->timing) {
+            for (int i = 0; i < chunk; ++i) TRY(iteration(h, L, B, kind, &marks));
+        } else {
+            CK(cudaGraphLaunch(h->graph.exec, h->work));
+            h->launches += h->graph.nodes;
+        }
+        total_iters += chunk;
+    }
+    return TOMO_OK;
+}
+
 tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_opts& o, float* zeta, float* phase,
                         tomo_frame_info* info, const double* c_scale = nullptr, const double* nu_scale = nullptr,
                         const double* prop_c = nullptr) {
@@ -1218,12 +1328,21 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             TRY(h2d(dT, BB));
             return TOMO_OK;
         };
+        // frames reported as breakdowns at the start (non-finite slopes or
+        // warm start) take no part: their residual columns are zeroed, so the
+        // Gram products drop them as dependent, and their result is the
+        // initial guess
+        std::vector<char> broken(B, 0);
         {
             std::vector<FrameState> tmp(B);
             CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
             CK(cudaStreamSynchronize(h->work));
-            for (int f = 0; f < B; ++f) tol2[f] = tmp[f].tol2;
+            for (int f = 0; f < B; ++f) {
+                tol2[f] = tmp[f].tol2;
+                broken[f] = tmp[f].status == TOMO_FRAME_BREAKDOWN;
+            }
         }
+        CK(zero_broken(L, B, h->N, h->st, h->r));
         block_iters = 0;
         bool done = false;
         while (!done) {
@@ -1237,7 +1356,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             bool converged = false;
             bool have_norms = false;
             while (!converged) {
-                if (block_iters >= (long long)o.max_iter) break;
+                if (block_iters >= (long long)o.max_iter || past_deadline(h)) break;
                 // P = W T_W (orthonormal columns), A P, and the Gram products with P
                 CK(block_combine(L, B, h->N, dTW, W, nullptr, h->p));
                 TRY(apply_A(h->p, h->Ap));
@@ -1250,6 +1369,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
                     const double* rrs = hv(dRR);
                     converged = true;
                     for (int f = 0; f < B; ++f) {
+                        if (broken[f]) continue;
                         double t = 0.0;
                         for (int q = 0; q < kNormSlices; ++q) t += rrs[(size_t)f * kNormSlices + q];
                         converged = converged && t <= tol2[f];
@@ -1298,52 +1418,21 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             std::vector<FrameState> tmp(B);
             CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
             CK(cudaStreamSynchronize(h->work));
-            for (auto& f : tmp) { f.active = 0; f.status = 0; }
+            for (auto& f : tmp) {
+                f.active = 0;
+                if (f.status != TOMO_FRAME_BREAKDOWN) f.status = 0;
+            }
             CK(cudaMemcpyAsync(h->st, tmp.data(), sizeof(FrameState) * B, cudaMemcpyHostToDevice, h->work));
             TRY(true_res(o.max_refine));
+            // a restart must not carry a non-finite residual column into the block
+            CK(zero_broken(L, B, h->N, h->st, h->r));
             CK(count_active(L, B, h->st, h->d_nactive));
             CK(cudaMemcpyAsync(h->h_nactive, h->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, h->work));
             CK(cudaStreamSynchronize(h->work));
             done = *h->h_nactive == 0;
         }
     }
-    const int chunk = std::max(1, o.check_every);
-    if (!h->timing && block_iters < 0) TRY(build_graph(h, B, chunk, kind));
-    long long total_iters = 0;
-    std::vector<std::pair<int, int>> marks;
-    for (; block_iters < 0;) {
-        CK(count_active(L, B, h->st, h->d_nactive));
-        CK(cudaMemcpyAsync(h->h_nactive, h->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, h->work));
-        CK(cudaStreamSynchronize(h->work));
-        if (h->timing) collect_timing(h, marks);
-        if (*h->h_nactive == 0) {
-            // FP64 true residual s - A zeta and restart of the frames above tol
-            TRY(true_res(o.max_refine));
-            CK(count_active(L, B, h->st, h->d_nactive));
-            CK(cudaMemcpyAsync(h->h_nactive, h->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, h->work));
-            CK(cudaStreamSynchronize(h->work));
-            if (*h->h_nactive == 0) break;
-        }
-        if (total_iters >= (long long)o.max_iter) {
-            // iteration budget spent: stop the remaining frames
-            std::vector<FrameState> tmp(B);
-            CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
-            CK(cudaStreamSynchronize(h->work));
-            for (auto& f : tmp)
-                if (f.active) { f.active = 0; f.status = TOMO_FRAME_MAXIT; }
-            CK(cudaMemcpyAsync(h->st, tmp.data(), sizeof(FrameState) * B, cudaMemcpyHostToDevice, h->work));
-            CK(cudaStreamSynchronize(h->work));
-            TRY(true_res(0));
-            break;
-        }
-        if (h->timing) {
-            for (int i = 0; i < chunk; ++i) TRY(iteration(h, L, B, kind, &marks));
-        } else {
-            CK(cudaGraphLaunch(h->graph.exec, h->work));
-            h->launches += h->graph.nodes;
-        }
-        total_iters += chunk;
-    }
+    if (block_iters < 0) TRY(run_iterations(h, L, B, o, kind, true_res));
     if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->x, nullptr, nullptr));
     if (prop_c) CK(scale_rows(L, B, h->N, h->d_rhs_scale, h->x, zeta));
     else CK(cudaMemcpyAsync(zeta, h->x, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
@@ -1371,8 +1460,190 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
     return TOMO_OK;
 }
 
+// Per-frame results of a solve into info_host (host array) from the FrameState.
+tomo_status report(tomo_handle* h, int B, tomo_frame_info* info) {
+    if (!info) return TOMO_OK;
+    std::vector<FrameState> tmp(B);
+    CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
+    CK(cudaStreamSynchronize(h->work));
+    for (int f = 0; f < B; ++f) {
+        h->frame_iters += tmp[f].iters;
+        info[f].iters = tmp[f].iters;
+        info[f].refinements = tmp[f].refinements;
+        info[f].status = tmp[f].status;
+        info[f].pad_ = 0;
+        info[f].relres = tmp[f].relres;
+    }
+    return TOMO_OK;
+}
+
+// FP64 conjugate gradients (Sec. 2.G) on B <= max_batch frames: FP64 slopes
+// s64 and solution zeta64 (device), the FP64 product of Eq. mvm_ss, FP64
+// vectors and scalars, the FP64 true residual at exit with restarts from it.
+tomo_status solve_chunk_f64(tomo_handle* h, const double* s64, int B, const tomo_solve_opts& o, double* zeta64,
+                            tomo_frame_info* info, const double* c_scale = nullptr, const double* nu_scale = nullptr) {
+    Launch L{h->work, &h->launches};
+    TRY(ensure_f64(h));
+    TRY(set_fscale(h, B, c_scale, nu_scale));
+    CK(cudaEventRecord(h->ev_in, h->stream));
+    CK(cudaStreamWaitEvent(h->work, h->ev_in, 0));
+    const int ms_len = 2 * h->n_vs;
+    const size_t BN = (size_t)B * h->N;
+    // right-hand side (M_s s under mode removal) in the handle's own buffer
+    CK(cudaMemcpyAsync(h->s64, s64, sizeof(double) * BN, cudaMemcpyDeviceToDevice, h->work));
+    if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->s64, nullptr, nullptr));
+    if (o.warm_start) {
+        CK(cudaMemcpyAsync(h->x64, zeta64, sizeof(double) * BN, cudaMemcpyDeviceToDevice, h->work));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->x64, nullptr, nullptr));
+        TRY(apply_ss64(h, L, h->x64, h->Ap64, B, h->d_fscale));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->Ap64, nullptr, nullptr));
+        CK(cg64_init(L, B, h->N, h->nparts, h->s64, h->Ap64, h->x64, h->r64, h->p64, h->Ap64, h->init_part));
+    } else {
+        CK(cg64_init(L, B, h->N, h->nparts, h->s64, nullptr, h->x64, h->r64, h->p64, h->Ap64, h->init_part));
+    }
+    CK(cg_init_scalars(L, B, h->nparts, h->init_part, o.tol, o.warm_start, h->st));
+    // FP64 true residual r = s - A x (the iterate is kept in range(M_s) under mode removal)
+    auto true_res = [&](int max_refine) -> tomo_status {
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->x64, nullptr, nullptr));
+        TRY(apply_ss64(h, L, h->x64, h->yd, B, h->d_fscale));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->yd, nullptr, nullptr));
+        CK(residual64(L, B, h->N, h->nparts, h->s64, h->yd, h->r64, h->res_part));
+        CK(true_residual_finalize(L, B, h->nparts, h->res_part, o.tol, max_refine, h->st));
+        return TOMO_OK;
+    };
+    TRY(run_iterations(h, L, B, o, kIterCG64, true_res));
+    CK(cudaMemcpyAsync(zeta64, h->x64, sizeof(double) * BN, cudaMemcpyDeviceToDevice, h->work));
+    CK(cudaEventRecord(h->ev_out, h->work));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_out, 0));
+    return report(h, B, info);
+}
+
+// Mixed-precision iterative refinement (tomo_solve_opts.precision =
+// TOMO_PREC_MIXED): zeta accumulated in FP64; each pass forms the FP64 true
+// residual r = s - A zeta with the FP64 operator and solves A d = r with the
+// FP32 solver of solve_chunk (any method) to a relative tolerance tau, then
+// zeta += d in FP64.  tau = o.inner_tol, or automatically the factor still
+// missing to tol (0.5 tol / max relres), at least 2e-5 (the floor FP32
+// storage sets) and at most 0.5.  Frames that meet tol get a zero right-hand
+// side in later passes (the inner solve then leaves them alone).  Slopes s32
+// (FP32) or s64 (FP64), one of them; output zeta32 or zeta64 (one of them),
+// phase as solve_chunk.  c_scale / nu_scale / prop_c as
+// solve_chunk; the outer operator of frame f is A_f = c_f pc_f Sigma_ss +
+// nu_f pc_f Sigma_eta_eta with pc_f = prop_c[f] (1 when null).
+tomo_status solve_chunk_mixed(tomo_handle* h, const float* s32, const double* s64, int B, const tomo_solve_opts& o,
+                              float* zeta32, double* zeta64, float* phase, tomo_frame_info* info,
+                              const double* c_scale = nullptr, const double* nu_scale = nullptr,
+                              const double* prop_c = nullptr) {
+    Launch L{h->work, &h->launches};
+    TRY(ensure_f64(h));
+    const int ms_len = 2 * h->n_vs;
+    const size_t BN = (size_t)B * h->N;
+    {
+        std::vector<double2> fs(B);
+        for (int f = 0; f < B; ++f) {
+            const double pc = prop_c ? prop_c[f] : 1.0;
+            fs[f] = make_double2((c_scale ? c_scale[f] : 1.0) * pc, (nu_scale ? nu_scale[f] : 1.0) * pc);
+        }
+        CK(cudaMemcpyAsync(h->d_fs_outer, fs.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, h->work));
+        CK(cudaStreamSynchronize(h->work));
+    }
+    CK(cudaEventRecord(h->ev_in, h->stream));
+    CK(cudaStreamWaitEvent(h->work, h->ev_in, 0));
+    if (s64) CK(cudaMemcpyAsync(h->s64, s64, sizeof(double) * BN, cudaMemcpyDeviceToDevice, h->work));
+    else CK(to_f64(L, BN, s32, h->s64));
+    if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->s64, nullptr, nullptr));
+    CK(norm2_64(L, B, h->N, h->nparts, h->s64, h->res_part, h->snorm64));
+    // initial guess
+    if (o.warm_start == 1) {
+        if (zeta64) CK(cudaMemcpyAsync(h->x64, zeta64, sizeof(double) * BN, cudaMemcpyDeviceToDevice, h->work));
+        else CK(to_f64(L, BN, zeta32, h->x64));
+    } else if (o.warm_start == 2) {
+        if (!h->ws.ready) return TOMO_EINVAL;
+        CK(f64_to_f32(L, B, h->N, nullptr, h->s64, h->rhs32));
+        for (int b0 = 0; b0 < B; b0 += h->ws.maxB) {
+            const int nb = std::min(h->ws.maxB, B - b0);
+            TRY(ws_forward(h, L, h->rhs32 + (size_t)b0 * h->N, nb, h->d32 + (size_t)b0 * h->N));
+        }
+        CK(to_f64(L, BN, h->d32, h->x64));
+    } else {
+        CK(cudaMemsetAsync(h->x64, 0, sizeof(double) * BN, h->work));
+    }
+    // the inner solves run under the call's deadline (h->deadline), which solve_chunk checks
+    tomo_solve_opts in = o;
+    in.precision = TOMO_PREC_FP32;
+    in.warm_start = 0;
+    std::vector<double> rel(B, 0.0);
+    std::vector<int> iters(B, 0), status(B, TOMO_FRAME_MAXIT), passes(B, 0);
+    std::vector<tomo_frame_info> inner(B);
+    long long used = 0;
+    for (int pass = 0;; ++pass) {
+        // FP64 true residual of the current zeta
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->x64, nullptr, nullptr));
+        TRY(apply_ss64(h, L, h->x64, h->yd, B, h->d_fs_outer));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->yd, nullptr, nullptr));
+        CK(residual64(L, B, h->N, h->nparts, h->s64, h->yd, h->r64, h->res_part));
+        CK(relres64(L, B, h->nparts, h->res_part, h->snorm64, h->rel64));
+        CK(cudaMemcpyAsync(rel.data(), h->rel64, sizeof(double) * B, cudaMemcpyDeviceToHost, h->work));
+        CK(cudaStreamSynchronize(h->work));
+        double worst = 0.0;
+        int left = 0;
+        for (int f = 0; f < B; ++f) {
+            if (status[f] == TOMO_FRAME_BREAKDOWN) continue;
+            if (!std::isfinite(rel[f])) { status[f] = TOMO_FRAME_BREAKDOWN; continue; }
+            if (rel[f] <= o.tol) { status[f] = TOMO_FRAME_CONVERGED; continue; }
+            status[f] = TOMO_FRAME_MAXIT;
+            ++left;
+            worst = std::max(worst, rel[f]);
+        }
+        if (left == 0 || pass > o.max_refine || used >= o.max_iter || past_deadline(h)) break;
+        // the next correction: frames above tol only (broken and converged frames get zeros)
+        for (int f = 0; f < B; ++f)
+            if (status[f] != TOMO_FRAME_MAXIT) rel[f] = 0.0;
+        CK(cudaMemcpyAsync(h->rel64, rel.data(), sizeof(double) * B, cudaMemcpyHostToDevice, h->work));
+        CK(inner_rhs(L, B, h->N, h->rel64, o.tol, h->r64, h->rhs32));
+        in.tol = o.inner_tol > 0 ? o.inner_tol : std::min(0.5, std::max(2e-5, 0.5 * o.tol / worst));
+        in.max_iter = (int)std::max<long long>(1, o.max_iter - used);
+        TRY(solve_chunk(h, h->rhs32, B, in, h->d32, nullptr, inner.data(), c_scale, nu_scale, prop_c));
+        int most = 0;
+        for (int f = 0; f < B; ++f) {
+            if (status[f] != TOMO_FRAME_MAXIT) continue;
+            iters[f] += inner[f].iters;
+            passes[f] += 1;
+            most = std::max(most, inner[f].iters);
+            if (inner[f].status == TOMO_FRAME_BREAKDOWN) status[f] = TOMO_FRAME_BREAKDOWN;
+        }
+        used += most;
+        CK(add_f32_to_f64(L, BN, h->d32, h->x64));
+    }
+    if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->x64, nullptr, nullptr));
+    if (zeta64) CK(cudaMemcpyAsync(zeta64, h->x64, sizeof(double) * BN, cudaMemcpyDeviceToDevice, h->work));
+    float* z32 = zeta32 ? zeta32 : h->rhs32;
+    if (zeta32 || phase) CK(f64_to_f32(L, B, h->N, nullptr, h->x64, z32));
+    if (phase) {
+        TRY(apply_os(h, L, z32, phase, B, h->d_fs_outer));
+        if (h->modes)
+            CK(mode_project<float>(L, B, h->n_vphi, h->n_targets, 1, h->d_Qp, nullptr, phase, nullptr, nullptr));
+    }
+    CK(cudaEventRecord(h->ev_out, h->work));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_out, 0));
+    CK(cudaStreamSynchronize(h->work));
+    if (info) {
+        for (int f = 0; f < B; ++f) {
+            info[f].iters = iters[f];
+            info[f].refinements = std::max(0, passes[f] - 1);
+            info[f].status = status[f];
+            info[f].pad_ = 0;
+            info[f].relres = rel[f];
+        }
+    }
+    return TOMO_OK;
+}
+
 tomo_status check_opts(const tomo_solve_opts& o, int max_batch = 0) {
     if (!(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 || o.check_every < 1) return TOMO_EINVAL;
+    if (o.precision != TOMO_PREC_FP32 && o.precision != TOMO_PREC_FP64 && o.precision != TOMO_PREC_MIXED)
+        return TOMO_EINVAL;
+    if (!(o.inner_tol >= 0) || !(o.inner_tol < 1) || !(o.deadline_ms >= 0)) return TOMO_EINVAL;
     if (o.method != TOMO_METHOD_CG && o.method != TOMO_METHOD_MINRES && o.method != TOMO_METHOD_BLOCK)
         return TOMO_EINVAL;
     if (o.method == TOMO_METHOD_MINRES && o.precond) return TOMO_EINVAL;
@@ -1390,7 +1661,32 @@ tomo_solve_opts default_opts() {
     o.check_every = 32;
     o.precond = 0;
     o.method = TOMO_METHOD_CG;
+    o.precision = TOMO_PREC_FP32;
+    o.inner_tol = 0.0;
+    o.deadline_ms = 0.0;
     return o;
+}
+
+// tomo_solve's work, without the per-call set-up (deadline) and status.
+tomo_status solve_impl(tomo_handle* h, const float* slopes, int batch, const tomo_solve_opts& o, float* zeta,
+                       float* phase, tomo_frame_info* info) {
+    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        const float* sb = slopes + (size_t)f0 * h->N;
+        float* zb = zeta + (size_t)f0 * h->N;
+        float* pb = phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr;
+        tomo_frame_info* ib = info ? info + f0 : nullptr;
+        if (o.precision == TOMO_PREC_MIXED) TRY(solve_chunk_mixed(h, sb, nullptr, B, o, zb, nullptr, pb, ib));
+        else TRY(solve_chunk(h, sb, B, o, zb, pb, ib));
+    }
+    return TOMO_OK;
+}
+
+tomo_status end_call(tomo_handle* h, tomo_status s) {
+    const bool late = h->timed_out;
+    h->has_deadline = false;
+    h->timed_out = false;
+    return s == TOMO_OK && late ? TOMO_ETIMEOUT : s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1402,11 +1698,15 @@ tomo_solve_opts default_opts() {
 // holds these 16 MiB until the process exits, and every call of the entry
 // point shares them.
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+constexpr int kMaxGridY = 65535;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Host code may not use g_noalloc_scratch as a device address (on the host it
 // is only a stand-in symbol); the device address is looked up once per device
-// with that device current.
+// with that device current.  The address is kept for the life of the process:
+// a cudaDeviceReset unloads the library's device code (and frees every
+// handle's memory, so no handle survives it either), after which this entry
+// point must not be called on that device again.
 constexpr int kNoAllocMaxDevices = 64;
 struct NoAllocDevice {
     std::once_flag once;
@@ -1449,7 +1749,9 @@ tomo_status tomo_apply_css_noalloc(tomo_handle* h, const float* x, float* y, int
     }
     void* scratch = nullptr;
     TRY(noalloc_scratch(&scratch));
-    const int chunk = (int)std::min<size_t>(kNoAllocScratchBytes / per_frame, (size_t)1 << 20);
+    // frames per chunk: as many as the buffer holds, at most kMaxGridY (every
+    // pass puts the frames of a launch on gridDim.y, which is limited to 65535)
+    const int chunk = (int)std::min<size_t>(kNoAllocScratchBytes / per_frame, (size_t)kMaxGridY);
     float2* X1 = static_cast<float2*>(scratch);
     float2* Y1 = X1 + (size_t)chunk * (half / sizeof(float2));
     Launch L = launch_of(h);
@@ -1560,7 +1862,8 @@ tomo_status tomo_reconstructor(tomo_handle* h, int target, const tomo_solve_opts
     tomo_solve_opts o = opts ? *opts : default_opts();
     TRY(check_opts(o, h->max_batch));
     if (o.warm_start) return TOMO_EINVAL;
-    if (h->modes) return TOMO_EINVAL;
+    if (h->modes || o.precision != TOMO_PREC_FP32) return TOMO_EINVAL;
+    begin_call(h, o);
     Launch L = launch_of(h);
     const int nv = h->n_vphi;
     double *dots = nullptr, *sums = nullptr;
@@ -1628,7 +1931,7 @@ tomo_status tomo_reconstructor(tomo_handle* h, int target, const tomo_solve_opts
             h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
         }
     }
-    return st;
+    return end_call(h, st);
 }
 
 tomo_status tomo_apply_reconstructor(tomo_handle* h, const float* R, int rows, const float* slopes, int batch,
@@ -1660,19 +1963,48 @@ tomo_status tomo_solve(tomo_handle* h, const float* slopes, int batch, const tom
     if (!h || !slopes || !zeta || batch < 0) return TOMO_EINVAL;
     tomo_solve_opts o = opts ? *opts : default_opts();
     TRY(check_opts(o, h->max_batch));
-    for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
-        const int B = std::min(h->max_batch, batch - f0);
-        TRY(solve_chunk(h, slopes + (size_t)f0 * h->N, B, o, zeta + (size_t)f0 * h->N,
-                        phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr, info ? info + f0 : nullptr));
-    }
-    return TOMO_OK;
+    if (o.precision == TOMO_PREC_FP64) return TOMO_EINVAL;     // FP64 buffers: tomo_solve_f64
+    begin_call(h, o);
+    return end_call(h, solve_impl(h, slopes, batch, o, zeta, phase, info));
 }
+
+tomo_status tomo_solve_f64(tomo_handle* h, const double* slopes, int batch, const tomo_solve_opts* opts,
+                           double* zeta, tomo_frame_info* info) {
+    if (!h || !slopes || !zeta || batch < 0) return TOMO_EINVAL;
+    tomo_solve_opts o = opts ? *opts : default_opts();
+    if (!opts) o.precision = TOMO_PREC_FP64;
+    TRY(check_opts(o, h->max_batch));
+    if (o.precision == TOMO_PREC_FP32 || o.warm_start == 2) return TOMO_EINVAL;
+    if (o.precision == TOMO_PREC_FP64 && (o.method != TOMO_METHOD_CG || o.precond)) return TOMO_EINVAL;
+    begin_call(h, o);
+    tomo_status st = TOMO_OK;
+    for (int f0 = 0; f0 < batch && st == TOMO_OK; f0 += h->max_batch) {
+        const int B = std::min(h->max_batch, batch - f0);
+        const double* sb = slopes + (size_t)f0 * h->N;
+        double* zb = zeta + (size_t)f0 * h->N;
+        tomo_frame_info* ib = info ? info + f0 : nullptr;
+        st = o.precision == TOMO_PREC_FP64 ? solve_chunk_f64(h, sb, B, o, zb, ib)
+                                           : solve_chunk_mixed(h, nullptr, sb, B, o, nullptr, zb, nullptr, ib);
+    }
+    return end_call(h, st);
+}
+
+tomo_status solve_r0_impl(tomo_handle* h, const float* slopes, int batch, const double* r0, const double* noise_scale,
+                          const tomo_solve_opts& o, float* zeta, float* phase, tomo_frame_info* info);
 
 tomo_status tomo_solve_r0(tomo_handle* h, const float* slopes, int batch, const double* r0, const double* noise_scale,
                           const tomo_solve_opts* opts, float* zeta, float* phase, tomo_frame_info* info) {
     if (!h || !slopes || !zeta || !r0 || batch < 0) return TOMO_EINVAL;
     tomo_solve_opts o = opts ? *opts : default_opts();
     TRY(check_opts(o, h->max_batch));
+    if (o.precision == TOMO_PREC_FP64) return TOMO_EINVAL;
+    begin_call(h, o);
+    return end_call(h, solve_r0_impl(h, slopes, batch, r0, noise_scale, o, zeta, phase, info));
+}
+
+tomo_status solve_r0_impl(tomo_handle* h, const float* slopes, int batch, const double* r0, const double* noise_scale,
+                          const tomo_solve_opts& o, float* zeta, float* phase, tomo_frame_info* info) {
+    const bool mixed = o.precision == TOMO_PREC_MIXED;
     // von Karman covariances scale as r0^{-5/3} (B(0) = c_v (L0 / r0)^{5/3})
     std::vector<double> c(batch);
     for (int f = 0; f < batch; ++f) {
@@ -1691,17 +2023,25 @@ tomo_status tomo_solve_r0(tomo_handle* h, const float* slopes, int batch, const 
         std::vector<double> one((size_t)h->max_batch, 1.0), kap((size_t)h->max_batch, kappa);
         for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
             const int B = std::min(h->max_batch, batch - f0);
-            TRY(solve_chunk(h, slopes + (size_t)f0 * h->N, B, o, zeta + (size_t)f0 * h->N,
-                            phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr, info ? info + f0 : nullptr,
-                            one.data(), kap.data(), c.data() + f0));
+            const float* sb = slopes + (size_t)f0 * h->N;
+            float* zb = zeta + (size_t)f0 * h->N;
+            float* pb = phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr;
+            tomo_frame_info* ib = info ? info + f0 : nullptr;
+            if (mixed) TRY(solve_chunk_mixed(h, sb, nullptr, B, o, zb, nullptr, pb, ib, one.data(), kap.data(),
+                                             c.data() + f0));
+            else TRY(solve_chunk(h, sb, B, o, zb, pb, ib, one.data(), kap.data(), c.data() + f0));
         }
         return TOMO_OK;
     }
     for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
         const int B = std::min(h->max_batch, batch - f0);
-        TRY(solve_chunk(h, slopes + (size_t)f0 * h->N, B, o, zeta + (size_t)f0 * h->N,
-                        phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr, info ? info + f0 : nullptr,
-                        c.data() + f0, noise_scale ? noise_scale + f0 : nullptr));
+        const float* sb = slopes + (size_t)f0 * h->N;
+        float* zb = zeta + (size_t)f0 * h->N;
+        float* pb = phase ? phase + (size_t)f0 * h->n_targets * h->n_vphi : nullptr;
+        tomo_frame_info* ib = info ? info + f0 : nullptr;
+        const double* nb = noise_scale ? noise_scale + f0 : nullptr;
+        if (mixed) TRY(solve_chunk_mixed(h, sb, nullptr, B, o, zb, nullptr, pb, ib, c.data() + f0, nb));
+        else TRY(solve_chunk(h, sb, B, o, zb, pb, ib, c.data() + f0, nb));
     }
     return TOMO_OK;
 }
@@ -1710,6 +2050,10 @@ tomo_status tomo_solve_host(tomo_handle* h, const float* slopes, int batch, cons
                             float* phase, tomo_frame_info* info) {
     if (!h || !slopes || !zeta || batch < 0) return TOMO_EINVAL;
     tomo_solve_opts o = opts ? *opts : default_opts();
+    TRY(check_opts(o, h->max_batch));
+    if (o.precision == TOMO_PREC_FP64) return TOMO_EINVAL;
+    begin_call(h, o);
+    tomo_status st = TOMO_OK;
     const size_t nphi = (size_t)h->n_targets * h->n_vphi;
     for (int f0 = 0; f0 < batch; f0 += h->max_batch) {
         const int B = std::min(h->max_batch, batch - f0);
@@ -1718,7 +2062,8 @@ tomo_status tomo_solve_host(tomo_handle* h, const float* slopes, int batch, cons
         if (o.warm_start)
             CK(cudaMemcpyAsync(h->z_stage, zeta + (size_t)f0 * h->N, sizeof(float) * B * h->N,
                                cudaMemcpyHostToDevice, h->stream));
-        TRY(tomo_solve(h, h->s_stage, B, &o, h->z_stage, phase ? h->phi_stage : nullptr, info ? info + f0 : nullptr));
+        st = solve_impl(h, h->s_stage, B, o, h->z_stage, phase ? h->phi_stage : nullptr, info ? info + f0 : nullptr);
+        if (st != TOMO_OK) break;
         CK(cudaMemcpyAsync(zeta + (size_t)f0 * h->N, h->z_stage, sizeof(float) * B * h->N, cudaMemcpyDeviceToHost,
                            h->stream));
         if (phase)
@@ -1726,7 +2071,7 @@ tomo_status tomo_solve_host(tomo_handle* h, const float* slopes, int batch, cons
                                cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
-    return TOMO_OK;
+    return end_call(h, st);
 }
 
 tomo_status tomo_ws_init(tomo_handle* h, int hidden, int max_batch, float in_scale, float out_scale,

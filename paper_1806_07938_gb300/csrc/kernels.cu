@@ -796,10 +796,13 @@ __global__ void k_cg_init_scalars(int B, int nparts, const double* __restrict__ 
     // the recursive (FP32) residual is driven below kInnerTol * tol so that the
     // FP64 true residual normally clears tol without a restart
     s.tol2 = (kInnerTol * tol) * (kInnerTol * tol) * ss;
-    s.relres = ss > 0.0 ? sqrt(rr / ss) : 0.0;
+    // a frame whose slopes (or warm start) hold a NaN or an infinity never
+    // iterates: it is reported as a breakdown, with the initial guess as result
+    const bool finite = isfinite(rr) && isfinite(ss);
+    s.relres = !finite ? nan("") : (ss > 0.0 ? sqrt(rr / ss) : 0.0);
     s.iters = 0;
-    s.active = (ss > 0.0 && rr > s.tol2) ? 1 : 0;
-    s.status = 0;
+    s.active = (finite && ss > 0.0 && rr > s.tol2) ? 1 : 0;
+    s.status = finite ? 0 : 2;  // TOMO_FRAME_BREAKDOWN
     s.refinements = 0;
     s.gamma = 0.0;
     s.fresh = 1;
@@ -1042,6 +1045,11 @@ __global__ void k_true_residual_finalize(int B, int nparts, const double* __rest
     for (int i = 0; i < nparts; ++i) rr += parts[(size_t)f * nparts + i];
     s.relres = sqrt(rr / s.snorm2);
     s.active = 0;
+    if (!isfinite(s.relres)) {
+        s.status = 2;  // TOMO_FRAME_BREAKDOWN: non-finite input or iterate
+        st[f] = s;
+        return;
+    }
     if (s.relres > tol && s.status == 0) {
         if (s.refinements < max_refine) {
             s.refinements += 1;
@@ -1076,6 +1084,20 @@ __global__ void k_count_active(int B, const FrameState* st, int* n_active) {
 
 cudaError_t count_active(const Launch& L, int B, const FrameState* st, int* n_active) {
     k_count_active<<<1, 256, 0, L.stream>>>(B, st, n_active);
+    count(L);
+    return cudaGetLastError();
+}
+
+// v[f] = 0 for the frames reported as breakdowns (keeps a non-finite frame out
+// of the block recurrences, whose Gram products mix every frame).
+__global__ void k_zero_broken(int N, const FrameState* __restrict__ st, float* __restrict__ v) {
+    const int f = blockIdx.y;
+    if (st[f].status != 2) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) v[(size_t)f * N + i] = 0.f;
+}
+
+cudaError_t zero_broken(const Launch& L, int B, int N, const FrameState* st, float* v) {
+    k_zero_broken<<<dim3(16, B), 256, 0, L.stream>>>(N, st, v);
     count(L);
     return cudaGetLastError();
 }

@@ -156,6 +156,29 @@ cudaError_t true_residual(const Launch& L, int B, int N, int nparts, const float
 cudaError_t true_residual_finalize(const Launch& L, int B, int nparts, const double* parts,
                                    double tol, int max_refine, FrameState* st);
 cudaError_t count_active(const Launch& L, int B, const FrameState* st, int* n_active);
+// v [B][N]: frames with status TOMO_FRAME_BREAKDOWN set to zero.
+cudaError_t zero_broken(const Launch& L, int B, int N, const FrameState* st, float* v);
+
+// --- FP64 solves and mixed-precision refinement (solve64.cu) --------------------
+// FP64 CG vectors [B][N]; partial sums [B][nparts] (r^T r, s^T s: [B][2][nparts]
+// for the init), dot_part [B][nparts][3] as the fused passes lay them out.
+cudaError_t cg64_init(const Launch& L, int B, int N, int nparts, const double* s, const double* Ax0, double* x,
+                      double* r, double* p, double* Ap, double* parts);
+cudaError_t cg64_update(const Launch& L, int B, int N, int nparts, const FrameState* st, double* x, double* r,
+                        double* p, const double* Ap, double* rr_part);
+cudaError_t cg64_dots(const Launch& L, int B, int N, int nparts, const FrameState* st, const double* p,
+                      const double* r, const double* Ap, double* dot_part);
+// r = s - Ax (r may be null), parts [B][nparts] of r^T r
+cudaError_t residual64(const Launch& L, int B, int N, int nparts, const double* s, const double* Ax, double* r,
+                       double* parts);
+// rhs [f] = (float) r[f] where rel[f] > tol, else 0
+cudaError_t inner_rhs(const Launch& L, int B, int N, const double* rel, double tol, const double* r, float* rhs);
+cudaError_t add_f32_to_f64(const Launch& L, size_t n, const float* d, double* x);
+// out [f] = (float)(scale[f] x[f]) (scale may be null)
+cudaError_t f64_to_f32(const Launch& L, int B, int N, const double* scale, const double* x, float* out);
+cudaError_t relres64(const Launch& L, int B, int nparts, const double* parts, const double* snorm2, double* rel);
+// out[f] = s[f]^T s[f] (parts: [B][nparts] scratch)
+cudaError_t norm2_64(const Launch& L, int B, int N, int nparts, const double* s, double* parts, double* out);
 
 // --- mode removal (modes.cu) -------------------------------------------------
 // y [B][nblk][len] <- y - Q^T (Q y) per (frame, block), Q [3][len] orthonormal

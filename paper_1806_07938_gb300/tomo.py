@@ -16,6 +16,7 @@ from . import _build
 
 TOMO_OK, TOMO_EINVAL, TOMO_ENOMEM, TOMO_ECUDA, TOMO_ETIMEOUT, TOMO_ERANGE = range(6)
 FRAME_CONVERGED, FRAME_MAXIT, FRAME_BREAKDOWN = range(3)
+PRECISIONS = {"fp32": 0, "fp64": 1, "mixed": 2}
 
 
 class tomo_gs(ctypes.Structure):
@@ -44,7 +45,8 @@ class tomo_layout_info(ctypes.Structure):
 class tomo_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int), ("precond", ctypes.c_int),
-                ("method", ctypes.c_int)]
+                ("method", ctypes.c_int), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("deadline_ms", ctypes.c_double)]
 
 
 class tomo_frame_info(ctypes.Structure):
@@ -57,7 +59,7 @@ FRAME_INFO_DTYPE = np.dtype([("iters", np.int32), ("refinements", np.int32), ("s
 
 EXPORTS = ("tomo_create", "tomo_layout", "tomo_apply_css", "tomo_apply_css_noalloc", "tomo_apply_css_f64",
            "tomo_apply_cos",
-           "tomo_solve", "tomo_solve_r0", "tomo_solve_host", "tomo_autotune_result",
+           "tomo_solve", "tomo_solve_r0", "tomo_solve_host", "tomo_solve_f64", "tomo_autotune_result",
            "tomo_apply_cos_adjoint", "tomo_reconstructor", "tomo_apply_reconstructor", "tomo_launch_count", "tomo_set_kernel_timing",
            "tomo_apply_precond", "tomo_ws_init", "tomo_ws_param_count", "tomo_ws_set_params", "tomo_ws_get_params", "tomo_ws_apply",
            "tomo_ws_gradient", "tomo_ws_train_step",
@@ -68,9 +70,13 @@ _lib = None
 
 
 class TomoError(RuntimeError):
-    def __init__(self, fn, status):
+    """A call returned a status other than TOMO_OK.  For TOMO_ETIMEOUT of a solve
+    the outputs were written anyway and ``info`` holds the per-frame results."""
+
+    def __init__(self, fn, status, info=None):
         super().__init__(f"{fn} failed: {lib().tomo_strerror(status).decode()} (status {status})")
         self.status = status
+        self.info = info
 
 
 def lib(path=None):
@@ -92,6 +98,7 @@ def lib(path=None):
     L.tomo_apply_cos.argtypes = [vp, vp, vp, i]
     L.tomo_solve.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
     L.tomo_solve_host.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
+    L.tomo_solve_f64.argtypes = [vp, vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp]
     L.tomo_autotune_result.argtypes = [vp, vp, vp, i, ctypes.POINTER(i)]
     L.tomo_apply_cos_adjoint.argtypes = [vp, vp, vp, i]
     L.tomo_reconstructor.argtypes = [vp, i, ctypes.POINTER(tomo_solve_opts), vp, vp, vp]
@@ -120,9 +127,9 @@ def lib(path=None):
     return L
 
 
-def _check(fn, status):
+def _check(fn, status, info=None):
     if status != TOMO_OK:
-        raise TomoError(fn, status)
+        raise TomoError(fn, status, info)
 
 
 def _dptr(t, dtype):
@@ -229,11 +236,15 @@ METHODS = {"cg": 0, "minres": 1, "block": 2}
 SLOPE_MODELS = {"hudgin": 0, "fried": 1}
 
 
-def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=0, check_every=32, precond=False, method="cg"):
+def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=0, check_every=32, precond=False, method="cg",
+               precision="fp32", inner_tol=0.0, deadline_ms=0.0):
     """warm_start: 0 cold, 1 zeta holds the guess, 2 the warm-start network's guess;
-    method: "cg", "minres" or "block" (block CG over the frames of a chunk)."""
+    method: "cg", "minres" or "block" (block CG over the frames of a chunk);
+    precision: "fp32", "fp64" (tomo_solve_f64 only) or "mixed" (FP64 outer
+    refinement around FP32 inner solves to inner_tol, 0 = automatic);
+    deadline_ms > 0: the call's wall-clock budget (TOMO_ETIMEOUT when spent)."""
     return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every, int(bool(precond)),
-                           METHODS[method])
+                           METHODS[method], PRECISIONS[precision], float(inner_tol), float(deadline_ms))
 
 
 def tomo_solve(h, slopes, batch, opts, zeta, phase=None):
@@ -242,7 +253,18 @@ def tomo_solve(h, slopes, batch, opts, zeta, phase=None):
     info = np.zeros(batch, FRAME_INFO_DTYPE)
     _check("tomo_solve", lib().tomo_solve(
         h, _dptr(slopes, torch.float32), batch, ctypes.byref(opts), _dptr(zeta, torch.float32),
-        _dptr(phase, torch.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)))
+        _dptr(phase, torch.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)), info)
+    return info
+
+
+def tomo_solve_f64(h, slopes, batch, opts, zeta):
+    """Device solve on FP64 slopes and zeta (opts.precision "fp64" or "mixed");
+    returns the per-frame info."""
+    import torch
+    info = np.zeros(batch, FRAME_INFO_DTYPE)
+    _check("tomo_solve_f64", lib().tomo_solve_f64(
+        h, _dptr(slopes, torch.float64), batch, ctypes.byref(opts), _dptr(zeta, torch.float64),
+        ctypes.c_void_p(info.ctypes.data)), info)
     return info
 
 
@@ -284,7 +306,7 @@ def tomo_solve_r0(h, slopes, batch, r0, opts, zeta, phase=None, noise_scale=None
     _check("tomo_solve_r0", lib().tomo_solve_r0(
         h, _dptr(slopes, torch.float32), batch, _hptr(r0, np.float64),
         _hptr(ns, np.float64) if ns is not None else None, ctypes.byref(opts), _dptr(zeta, torch.float32),
-        _dptr(phase, torch.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)))
+        _dptr(phase, torch.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)), info)
     return info
 
 
@@ -293,7 +315,7 @@ def tomo_solve_host(h, slopes, batch, opts, zeta, phase=None):
     info = np.zeros(batch, FRAME_INFO_DTYPE)
     _check("tomo_solve_host", lib().tomo_solve_host(
         h, _hptr(slopes, np.float32), batch, ctypes.byref(opts), _hptr(zeta, np.float32),
-        _hptr(phase, np.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)))
+        _hptr(phase, np.float32) if phase is not None else None, ctypes.c_void_p(info.ctypes.data)), info)
     return info
 
 

@@ -479,16 +479,42 @@ def elt():
     return cfg, full[..., mask].reshape(8, -1)
 
 
+def elt_rows(n, eps, NP, seed):
+    """Rows of the ELT system to check against the oracle: three per
+    (guide star, slope component) plane, a pupil-edge subaperture (cycling
+    through the top, bottom, left and right edges), an obstruction-edge one
+    (cycling through the four that touch the central obstruction on its
+    axes) and a random one."""
+    mask = geo.subaperture_mask(n, eps)
+    ii, jj = np.nonzero(mask)                               # row-major, as the vectors are laid out
+    nv = len(ii)
+    mid = n // 2
+    in_mid = np.nonzero(ii == mid)[0]
+    edge = [0, nv - 1, int(in_mid[0]), int(in_mid[-1])]
+    gap = np.nonzero(np.diff(jj[in_mid]) > 1)[0][0]         # the obstruction splits the middle row
+    in_col = np.nonzero(jj == mid)[0]
+    gapc = np.nonzero(np.diff(ii[in_col]) > 1)[0][0]
+    obst = [int(in_mid[gap]), int(in_mid[gap + 1]), int(in_col[gapc]), int(in_col[gapc + 1])]
+    rng = np.random.default_rng(seed)
+    rows = []
+    for q in range(NP):
+        rows += [q * nv + edge[q % 4], q * nv + obst[q % 4], q * nv + int(rng.integers(nv))]
+    return np.array(rows)
+
+
 def test_elt_css_sampled_rows(T, elt):
     cfg, s = elt
     with Handle(T, cfg, max_batch=8) as H:
         assert H.info.P == 150 and H.info.N == 47664
         x = np.random.default_rng(9).standard_normal((8, H.info.N))
         y = H.css(x)
-        rows = np.random.default_rng(10).choice(H.info.N, 8, replace=False)
+        y64 = H.css(x, f64=True)
+        rows = elt_rows(cfg["n"], cfg["obstruction"], 2 * len(cfg["gs"]), 10)
+        assert len(set((r // H.info.n_vs) for r in rows)) == 12          # every (guide star, component) block
         ref = x @ cov.css_rows(cfg, rows).T + x[:, rows] * cov.noise_variance(cfg)[rows]
         scale = np.sqrt(np.mean(y ** 2))
         assert np.abs(y[:, rows] - ref).max() <= 1e-5 * scale
+        assert np.abs(y64[:, rows] - ref).max() <= 1e-11 * scale
 
 
 @pytest.mark.parametrize("pcg", [False, True])
@@ -498,15 +524,186 @@ def test_elt_solve_sampled_residual(T, elt, pcg):
         z, phi, info = H.solve(s, tol=1e-4, precond=pcg)
         print("ELT", "PCG" if pcg else "CG", info)
         assert (info["status"] == 0).all() and (info["relres"] <= 1e-4).all()
-        rows = np.random.default_rng(11).choice(H.info.N, 16, replace=False)
+        # the full residual of the returned zeta with the library's FP64
+        # product, whose rows are pinned to the oracle's here: the sampled
+        # rows of A zeta agree to FP64 rounding, so the full-vector residual
+        # below is the oracle's too
+        Az = H.css(z, f64=True)
+        rows = elt_rows(cfg["n"], cfg["obstruction"], 2 * len(cfg["gs"]), 11)
         Arows = cov.css_rows(cfg, rows)
-        Arows[np.arange(16), rows] += cov.noise_variance(cfg)[rows]
-        r = s[:, rows] - z @ Arows.T
-        # sampled estimate of ||s - A z|| / ||s||; the 16 rows give a rough estimate
-        est = np.sqrt((r ** 2).mean(axis=1) * H.info.N) / np.linalg.norm(s, axis=1)
-        assert (est <= 5e-4).all(), est
-        # projection rows
-        prow = np.array([0, 1000, 2080, 4159])
+        Arows[np.arange(len(rows)), rows] += cov.noise_variance(cfg)[rows]
+        ref = z @ Arows.T
+        assert np.abs(Az[:, rows] - ref).max() <= 1e-11 * np.sqrt(np.mean(Az ** 2))
+        s32 = s.astype(np.float32).astype(np.float64)         # the slopes the library solved for
+        rel = np.linalg.norm(s32 - Az, axis=1) / np.linalg.norm(s32, axis=1)
+        assert (rel <= 1e-4).all(), rel
+        assert np.allclose(rel, info["relres"], rtol=1e-6, atol=0)
+        # projection rows: pupil-edge and obstruction-edge phase points and two others
+        pm = geo.phase_point_mask(cfg["n"], cfg["obstruction"])
+        pi, pj = np.nonzero(pm)
+        c = cfg["n"] / 2.0
+        d2 = (pi - c) ** 2 + (pj - c) ** 2
+        prow = np.array([0, len(pi) - 1, int(np.argmin(d2)), int(np.argmax(d2)), 1000, 2080])
         Fr = cov.cos_interp_rows(cfg, 0, prow)
         ref = z @ Fr.T
         assert np.abs(phi[:, 0, prow] - ref).max() <= 1e-4 * np.abs(phi[:, 0]).max()
+
+
+# --------------------------------------------------------------------------- failure handling
+@pytest.mark.parametrize("method,pcg", [("cg", False), ("cg", True), ("minres", False), ("block", False),
+                                        ("block", True)])
+def test_nonfinite_frame_is_breakdown(T, method, pcg):
+    # a frame whose slopes hold a NaN or an infinity (a dead detector pixel,
+    # a corrupted transfer) is reported as a breakdown and returns its initial
+    # guess; the other frames of the batch, including those that share a block
+    # with it (the column pass takes up to 8 frames per block, block CG one
+    # Krylov space for all), converge to the oracle's solution
+    g = golden("lgs_mid")
+    s = g["s"].copy()
+    s[1, 17] = np.nan
+    s[2, 5] = np.inf
+    with Handle(T, g["cfg"], max_batch=4, precond=pcg) as H:
+        z, phi, info = H.solve(s, tol=1e-5, max_iter=20000, max_refine=3, precond=pcg, method=method)
+        print(method, pcg, info)
+        assert (info["status"][[1, 2]] == T.FRAME_BREAKDOWN).all(), info
+        assert (z[[1, 2]] == 0).all() and (phi[[1, 2]] == 0).all()
+        ok = [0, 3]
+        assert (info["status"][ok] == T.FRAME_CONVERGED).all() and (info["relres"][ok] <= 1e-5).all(), info
+        assert np.isfinite(z[ok]).all() and np.isfinite(phi[ok]).all()
+        err = np.linalg.norm(z[ok] - g["zeta"][ok], axis=1)
+        bound = info["relres"][ok] * np.linalg.norm(g["s"][ok], axis=1) / min(g["noise_sigma"]) ** 2
+        assert (err <= bound).all()
+
+
+def test_fp64_restart_fires(T):
+    # the FP64 true residual drives iterative refinement: a warm start 1e4
+    # times larger than the solution makes the recursive FP32 residual
+    # r0 = s - A x0 lose about 1e-7 * |A x0| / |s| of its accuracy, so CG's
+    # recursive residual reaches its target while the true one is still
+    # above tol; the solve must restart from the FP64 residual (at least once)
+    # and still end within the rigorous error bound of the Cholesky solution
+    g = golden("lgs_mid")
+    with Handle(T, g["cfg"], max_batch=4) as H:
+        x0 = 1e4 * np.random.default_rng(4).standard_normal(g["s"].shape) * np.abs(g["zeta"]).max()
+        sd = dev(g["s"])
+        zd = dev(x0)
+        info = T.tomo_solve(H.h, sd, 4, T.solve_opts(tol=1e-5, max_iter=40000, max_refine=6, warm_start=1,
+                                                     check_every=1), zd)
+        torch.cuda.synchronize()
+        z = zd.double().cpu().numpy()
+        print("restart", info)
+        assert (info["refinements"] >= 1).all(), info
+        assert (info["status"] == 0).all() and (info["relres"] <= 1e-5).all()
+        err = np.linalg.norm(z - g["zeta"], axis=1)
+        bound = info["relres"] * np.linalg.norm(g["s"], axis=1) / min(g["noise_sigma"]) ** 2
+        assert (err <= bound).all()
+
+
+# --------------------------------------------------------------------------- precision
+@pytest.mark.parametrize("name", ["ngs8m", "lgs_mid"])
+def test_fp64_solve_golden(T, name):
+    # FP64 throughout (BASELINE's 8 m configuration is stated in FP64): CG with
+    # the FP64 product to a relative residual of 1e-10, against the golden
+    # Cholesky solution, within the rigorous bound ||z - z*|| <= ||s - A z|| / sigma^2
+    g = golden(name)
+    with Handle(T, g["cfg"], max_batch=4) as H:
+        sd = dev(g["s"], torch.float64)
+        zd = torch.zeros_like(sd)
+        info = T.tomo_solve_f64(H.h, sd, 4, T.solve_opts(tol=1e-10, max_iter=20000, max_refine=3,
+                                                         precision="fp64"), zd)
+        torch.cuda.synchronize()
+        z = zd.cpu().numpy()
+        print(name, "FP64 CG", info)
+        assert (info["status"] == 0).all() and (info["relres"] <= 1e-10).all()
+        # the oracle's residual of the returned zeta: the FP64 operators differ
+        # by ~1e-14 relative, i.e. up to ~1e-14 cond(A) in the residual
+        assert np.allclose(info["relres"], solve.relative_residual(cov.system_matrix(g["cfg"]), g["s"].T, z.T),
+                           rtol=0.05, atol=2e-11)
+        err = np.linalg.norm(z - g["zeta"], axis=1)
+        bound = info["relres"] * np.linalg.norm(g["s"], axis=1) / min(g["noise_sigma"]) ** 2
+        assert (err <= bound + 1e-12 * np.linalg.norm(g["zeta"], axis=1)).all()
+        assert relL2(z, g["zeta"]) <= 1e-7
+        # options outside the FP64 path are rejected
+        for bad in (dict(precision="fp32"), dict(precision="fp64", method="minres"),
+                    dict(precision="fp64", precond=True), dict(precision="fp64", warm_start=2)):
+            with pytest.raises(T.TomoError):
+                T.tomo_solve_f64(H.h, sd, 4, T.solve_opts(**bad), zd)
+        with pytest.raises(T.TomoError):                       # FP64 needs FP64 buffers
+            H.solve(g["s"], precision="fp64")
+
+
+@pytest.mark.parametrize("name,method,pcg", [("ngs8m", "cg", False), ("lgs_mid", "cg", True),
+                                             ("lgs_mid", "block", True), ("lgs_mid", "minres", False)])
+def test_mixed_precision_reaches_fp64_residuals(T, name, method, pcg):
+    # mixed precision: FP32 inner solves (any method), FP64 accumulation of
+    # zeta and FP64 true residuals in the outer loop; it reaches 1e-10, far
+    # below the ~1e-5 floor of FP32 storage, after a few outer passes
+    g = golden(name)
+    with Handle(T, g["cfg"], max_batch=4, precond=pcg) as H:
+        sd = dev(g["s"], torch.float64)
+        zd = torch.zeros_like(sd)
+        info = T.tomo_solve_f64(H.h, sd, 4, T.solve_opts(tol=1e-10, max_iter=40000, max_refine=8, precision="mixed",
+                                                         method=method, precond=pcg), zd)
+        torch.cuda.synchronize()
+        z = zd.cpu().numpy()
+        print(name, method, "mixed", info)
+        assert (info["status"] == 0).all() and (info["relres"] <= 1e-10).all()
+        assert (info["refinements"] >= 1).all()
+        A = cov.system_matrix(g["cfg"])
+        assert np.allclose(info["relres"], solve.relative_residual(A, g["s"].T, z.T), rtol=0.05, atol=2e-11)
+        err = np.linalg.norm(z - g["zeta"], axis=1)
+        bound = info["relres"] * np.linalg.norm(g["s"], axis=1) / min(g["noise_sigma"]) ** 2
+        assert (err <= bound + 1e-12 * np.linalg.norm(g["zeta"], axis=1)).all()
+        assert relL2(z, g["zeta"]) <= 1e-7
+
+
+def test_mixed_precision_fp32_buffers(T):
+    # the same refinement behind tomo_solve (FP32 slopes, zeta rounded to FP32
+    # on output, projection from it), and behind tomo_solve_r0 (per-frame r0)
+    g = golden("lgs_mid")
+    with Handle(T, g["cfg"], max_batch=4) as H:
+        z, phi, info = H.solve(g["s"], tol=1e-7, max_iter=40000, max_refine=6, precision="mixed")
+        print("mixed FP32 out", info)
+        assert (info["status"] == 0).all() and (info["relres"] <= 1e-7).all()
+        # FP32 rounding of the output: within a few ulps of the Cholesky solution
+        assert relL2(z, g["zeta"]) <= 1e-6
+        ref = solve.remove_piston(g["phi_interp"].T).T
+        rms = [NM_PER_RAD * np.sqrt(np.mean((solve.remove_piston(phi[f, 0]) - ref[f]) ** 2)) for f in range(4)]
+        assert max(rms) <= 0.01, rms
+        cfg = g["cfg"]
+        r0 = np.array([0.10, 0.133, 0.167, 0.20])
+        zd = torch.zeros_like(dev(g["s"]))
+        info = T.tomo_solve_r0(H.h, dev(g["s"]), 4, r0, T.solve_opts(tol=1e-7, max_iter=40000, max_refine=6,
+                                                                     precision="mixed"), zd)
+        torch.cuda.synchronize()
+        z = zd.double().cpu().numpy()
+        assert (info["status"] == 0).all() and (info["relres"] <= 1e-7).all()
+        for f in range(4):
+            zs = solve.solve_cholesky(cov.system_matrix_r0(cfg, r0[f], 1.0), g["s"][f])
+            # the rigorous bound (lambda_min >= sigma^2: the noise term is not
+            # scaled here) plus the FP32 rounding of the output
+            bound = info["relres"][f] * np.linalg.norm(g["s"][f]) / min(g["noise_sigma"]) ** 2
+            assert np.linalg.norm(z[f] - zs) <= bound + 1e-6 * np.linalg.norm(zs)
+
+
+def test_deadline_returns_etimeout(T):
+    # a wall-clock budget (a real-time frame deadline): when it is spent the
+    # frames still iterating stop with their current iterate, reported as
+    # MAXIT, and the call returns TOMO_ETIMEOUT with the outputs written; a
+    # budget that suffices changes nothing
+    g = golden("lgs_mid")
+    with Handle(T, g["cfg"], max_batch=4, precond=True) as H:
+        for method in ("cg", "block"):
+            with pytest.raises(T.TomoError) as e:
+                H.solve(g["s"], tol=1e-5, precond=True, method=method, deadline_ms=1e-3)
+            assert e.value.status == T.TOMO_ETIMEOUT
+            info = e.value.info
+            assert (info["status"] == T.FRAME_MAXIT).all() and (info["relres"] > 1e-5).all(), info
+            assert np.isfinite(info["relres"]).all()
+            z, _, ok = H.solve(g["s"], tol=1e-5, precond=True, method=method, deadline_ms=1e5)
+            assert (ok["status"] == 0).all() and (ok["relres"] <= 1e-5).all()
+        sd = dev(g["s"], torch.float64)
+        with pytest.raises(T.TomoError) as e:
+            T.tomo_solve_f64(H.h, sd, 4, T.solve_opts(tol=1e-10, precision="mixed", deadline_ms=1e-3),
+                             torch.zeros_like(sd))
+        assert e.value.status == T.TOMO_ETIMEOUT and (e.value.info["status"] == T.FRAME_MAXIT).all()

@@ -67,6 +67,37 @@ def test_forward_and_gradient_match_oracle(T, n, hidden, B, hybrid):
         T.tomo_destroy(h)
 
 
+def test_adam_steps_match_oracle(T):
+    # tomo_ws_train_step is the gradient (checked above) followed by one Adam
+    # step (Kingma & Ba 2015): two steps in a row, each against
+    # oracle.cnn.adam_step applied to the same gradient, the oracle carrying
+    # its own moment estimates from step to step
+    cfg = small_cfg(n=7, n_gs=2, lgs=True, obstruction=0.2, D=0.527 * 7)
+    B, hidden, lr = 3, 5, 1e-2
+    h = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=B)
+    try:
+        info, _, _ = T.tomo_layout(h)
+        T.tomo_ws_init(h, hidden=hidden, max_batch=B, in_scale=0.5, out_scale=2.0)
+        T.tomo_ws_set_params(h, init_params(4, hidden, seed=3, last_gain=1.0))   # also resets m, v and t
+        rng = np.random.default_rng(8)
+        m = v = 0.0
+        for t in (1, 2):
+            sd = torch.tensor(rng.standard_normal((B, info.N)).astype(np.float32), device="cuda")
+            td = torch.tensor(rng.standard_normal((B, info.N)).astype(np.float32), device="cuda")
+            p_prev = T.tomo_ws_get_params(h).astype(np.float64)
+            g, _ = T.tomo_ws_gradient(h, sd, td, B)           # the gradient the step uses (no update)
+            p_exp, m, v = cnn.adam_step(p_prev, g, m, v, t, lr)
+            T.tomo_ws_train_step(h, sd, td, B, lr)
+            p = T.tomo_ws_get_params(h).astype(np.float64)
+            # every parameter within 1e-5 of the oracle's (the steps are about
+            # lr = 1e-2 each, so this is 1e-3 of a step)
+            print("adam step", t, "max |p - p_oracle|", np.abs(p - p_exp).max())
+            assert np.abs(p - p_exp).max() <= 1e-5
+            assert np.abs(p - p_prev).max() > 0.5 * lr
+    finally:
+        T.tomo_destroy(h)
+
+
 def test_training_gains_iterations(T):
     from paper_1806_07938_gb300 import workloads as W
     cfg = W.config("lgs_mid")
