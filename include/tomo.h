@@ -41,8 +41,12 @@
  * (separate handles are independent, on one device or several). 
  *
  * Errors: every call returns a tomo_status; on failure nothing is written to
- * the outputs that the caller can rely on.  Per-frame non-convergence is not
- * an error: it is reported in tomo_frame_info.status.
+ * the outputs that the caller can rely on, except TOMO_ETIMEOUT from a solve
+ * whose opts.deadline_ms ran out, which writes its outputs and per-frame
+ * information as a normal return would.  A solve also returns TOMO_ETIMEOUT
+ * when a bounded wait inside a kernel expired (a bulk copy that did not
+ * complete; the kernel then returns early instead of hanging).  Per-frame
+ * non-convergence is not an error: it is reported in tomo_frame_info.status.
  */
 #ifndef TOMO_H
 #define TOMO_H

@@ -91,21 +91,28 @@ def _layer_positions(cfg, pts, gsidx, k):
     return gam[:, None, None] * pts + h * alpha[:, None, :]
 
 
-def css_rows(cfg, rows):
-    """Rows ``rows`` of the noiseless Sigma_ss (FP64), shape (len(rows), N)."""
+def css_block(cfg, rows, cols):
+    """The entries (rows x cols) of the noiseless Sigma_ss (FP64), shape
+    (len(rows), len(cols)): the point-covariance sum above for those slopes."""
     pts, w, gsidx = slope_points(cfg)
     rows = np.asarray(rows, dtype=np.int64)
-    out = np.zeros((len(rows), len(pts)))
+    cols = np.asarray(cols, dtype=np.int64)
+    out = np.zeros((len(rows), len(cols)))
     for k, (h, frac) in enumerate(cfg["layers"]):
         r0k = turb.layer_r0(cfg["r0"], frac)
         pos = _layer_positions(cfg, pts, gsidx, k)
         K = pts.shape[1]
         for u in range(K):
             for v in range(K):
-                diff = pos[rows, u][:, None, :] - pos[None, :, v, :]
+                diff = pos[rows, u][:, None, :] - pos[cols, v][None, :, :]
                 rho = np.sqrt(diff[..., 0] ** 2 + diff[..., 1] ** 2)
-                out += (w[rows, u][:, None] * w[None, :, v]) * turb.vk_covariance(rho, r0k, cfg["L0"])
+                out += (w[rows, u][:, None] * w[cols, v][None, :]) * turb.vk_covariance(rho, r0k, cfg["L0"])
     return out
+
+
+def css_rows(cfg, rows):
+    """Rows ``rows`` of the noiseless Sigma_ss (FP64), shape (len(rows), N)."""
+    return css_block(cfg, rows, np.arange(slope_points(cfg)[0].shape[0]))
 
 
 def css_dense(cfg, block=512):

@@ -292,6 +292,19 @@ tomo_status apply_ss64(tomo_handle* h, const Launch& L, const double* x, double*
     return TOMO_OK;
 }
 
+// A bounded wait of a kernel (a bulk copy's mbarrier) that expired since the
+// last check is reported as TOMO_ETIMEOUT (the flag is per device).  Call after
+// the work has been synchronised.
+tomo_status check_wait_error() {
+    int flag = 0;
+    CK(take_wait_error(&flag));
+    if (flag) {
+        std::fprintf(stderr, "tomo: a bounded device wait expired (a bulk copy did not complete)\n");
+        return TOMO_ETIMEOUT;
+    }
+    return TOMO_OK;
+}
+
 // Wall-clock budget of a solve call (tomo_solve_opts.deadline_ms).
 void begin_call(tomo_handle* h, const tomo_solve_opts& o) {
     h->timed_out = false;
@@ -1447,6 +1460,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         std::vector<FrameState> tmp(B);
         CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
         CK(cudaStreamSynchronize(h->work));
+        TRY(check_wait_error());
         for (int f = 0; f < B; ++f) {
             if (block_iters >= 0) tmp[f].iters = (int)block_iters;
             h->frame_iters += tmp[f].iters;
@@ -1466,6 +1480,7 @@ tomo_status report(tomo_handle* h, int B, tomo_frame_info* info) {
     std::vector<FrameState> tmp(B);
     CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
     CK(cudaStreamSynchronize(h->work));
+    TRY(check_wait_error());
     for (int f = 0; f < B; ++f) {
         h->frame_iters += tmp[f].iters;
         info[f].iters = tmp[f].iters;
@@ -2071,6 +2086,7 @@ tomo_status tomo_solve_host(tomo_handle* h, const float* slopes, int batch, cons
                                cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    if (st == TOMO_OK) st = check_wait_error();
     return end_call(h, st);
 }
 

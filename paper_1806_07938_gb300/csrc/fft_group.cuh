@@ -324,8 +324,12 @@ __device__ __forceinline__ void fft_rounds(C* base, int gstride, int count, cons
     }
 }
 
-// Fills the __constant__ twiddle tables (host side, once per device).
-inline cudaError_t init_fft_constants() {
+// Fills the __constant__ twiddle tables (host side, once per device).  The
+// library is compiled without relocatable device code, so every translation
+// unit that includes this header has its own tables and must call this; the
+// function is static so that each unit's call fills that unit's tables (an
+// inline function would be merged into one definition by the linker).
+static cudaError_t init_fft_constants() {
     const double pi = 3.14159265358979323846;
     cudaError_t e = cudaSuccess;
 #define TOMO_TW_FILL(R)                                                                  \

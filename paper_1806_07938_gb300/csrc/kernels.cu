@@ -17,9 +17,11 @@
 // The 1/P^2 of the inverse transform is folded into the spectra K.
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "fft_group.cuh"
 #include "kernels.cuh"
+#include "rowpass.cuh"
 
 namespace tomo {
 
@@ -60,9 +62,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Row-forward pass
 // ---------------------------------------------------------------------------
 // Row pair (2j, 2j+1) of a plane is packed as one complex sequence
-// z = row_2j + i row_2j+1 in F[j][0..P); rows are padded to an odd stride so
-// that the column-wise accesses of the transposed write are conflict-free.
-__host__ __device__ constexpr int row_stride(int P) { return P | 1; }
+// z = row_2j + i row_2j+1 in F[j][0..P) (row_stride, rowpass.cuh).
 
 template <typename T, typename TIn, int PC>
 __global__ void __launch_bounds__(kThreads, TOMO_MIN_BLOCKS)
@@ -93,7 +93,9 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
     // sweep over the plane's valid entries (W_s^T scatter), with the CG update
     const size_t vbase = ((size_t)f * g.NPin + q) * mt.n_vs;
     const bool cgm = cg.p != nullptr;
-    double rr = 0.0;
+    // r^T r: each thread's ~16 products summed in the vector type (FP32 in the
+    // solver: GB300's FP64 rate is ~1/64 of its FP32 rate), FP64 across threads
+    T rr = 0;
     float* __restrict__ vx = cg.x;
     float* __restrict__ vr = cg.r;
     float* __restrict__ vp = cg.p;
@@ -117,7 +119,7 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
             }
             const float pn = re + beta * pe;
             vp[i] = pn;
-            rr += (double)re * re;
+            rr = fma((T)re, (T)re, rr);
             const int row = rc >> 16, col = rc & 0xffff;
             T* dst = reinterpret_cast<T*>(F + ((row >> 1) - pb) * RS + col) + (row & 1);
             *dst = (T)pn;
@@ -138,7 +140,7 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
             }
             vp[i] = pn;
             vAp[i] = apn;
-            rr += (double)re * re;
+            rr = fma((T)re, (T)re, rr);
             const int row = rc >> 16, col = rc & 0xffff;
             T* dst = reinterpret_cast<T*>(F + ((row >> 1) - pb) * RS + col) + (row & 1);
             *dst = (T)re;
@@ -159,7 +161,7 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
             }
             vp[i] = pn;
             vAp[i] = sn;
-            rr += (double)re * re;
+            rr = fma((T)re, (T)re, rr);
             const int row = rc >> 16, col = rc & 0xffff;
             T* dst = reinterpret_cast<T*>(F + ((row >> 1) - pb) * RS + col) + (row & 1);
             *dst = (T)re;
@@ -186,7 +188,7 @@ k_rows_fwd(MvmGeom g, MaskTables mt, const TIn* __restrict__ x, CgVecs cg, const
         for (int gi = warp; gi < ngrp; gi += kWarps)
             fft_g<PC, C, true>(F + gi * G * RS, RS, G, g.plan, tw, scr + warp * P, lane, n, P);
     if (cgm) {
-        const double t = block_sum<T>(rr, red);
+        const double t = block_sum<T>((double)rr, red);
         if (threadIdx.x == 0) cg.rr_part[((size_t)f * g.NPin + q) * gridDim.z + blockIdx.z] = t;
     }
     __syncthreads();
@@ -219,6 +221,13 @@ cudaError_t rows_fwd(const Launch& L, const MvmGeom& g, const MaskTables& mt, in
                      const FrameState* st, cplx_t<T>* X1T, const cplx_t<T>* tw, int rg) {
     const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     if (rg != 1 && rg != row_groups(g.n)) return cudaErrorInvalidValue;
+    if constexpr (std::is_same<T, float>::value && std::is_same<TIn, float>::value) {
+        if (rg == 1) {
+            bool used = false;
+            const cudaError_t e = rows_fwd_pp(L, g, mt, B, x, cg, st, X1T, tw, g_max_smem, &used);
+            if (e != cudaSuccess || used) return e;
+        }
+    }
     const size_t smem = rows_smem<T>(g, rg == 1 ? g.n : 2 * kRowPairsPerBlock);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
 #define TOMO_L(PC)                                                                                      \
@@ -557,20 +566,10 @@ __device__ __forceinline__ void pack_row_pair(const C* S, int m, int r, int P, i
 }
 
 // Loads the half spectra [kx][row] of the m kept rows of one plane into F as
-// packed row pairs z_k = A_k + i B_k over the full k range (Hermitian
-// extension; DC and Nyquist taken real), so that one inverse complex FFT per
-// pair returns row 2j in .x and row 2j+1 in .y.
-template <typename C>
-__device__ __forceinline__ void put_row_pair(C* F, int RS, int P, int j, int k, C a, C b) {
-    if (k == 0 || 2 * k == P) { a.y = 0; b.y = 0; }
-    F[j * RS + k] = cmk<C>(a.x - b.y, a.y + b.x);
-    if (k != 0 && 2 * k != P) {
-        const C ac = cconj(a), bc = cconj(b);
-        F[j * RS + P - k] = cmk<C>(ac.x - bc.y, ac.y + bc.x);
-    }
-}
-
-// Pairs [pb, pb + npair) of the plane go to F rows [0, npair).
+// packed row pairs z_k = A_k + i B_k over the full k range (put_row_pair,
+// rowpass.cuh), so that one inverse complex FFT per pair returns row 2j in .x
+// and row 2j+1 in .y.  Pairs [pb, pb + npair) of the plane go to F rows
+// [0, npair).
 template <typename C>
 __device__ __forceinline__ void load_row_pairs(const C* __restrict__ src, int m, int P, int nh, int RS, C* F,
                                                int pb, int npair) {
@@ -647,7 +646,9 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
     // second partner of the partial sums: r (CG, PCG) or the direction's A p (MINRES)
     const float* __restrict__ vr = cg.mode == 3 ? cg.Ap : cg.r;
     const int* __restrict__ rowcol = mt.rowcol;
-    double acc = 0.0, acc_r = 0.0, acc_a = 0.0;
+    // partial sums: each thread's ~16 products in the vector type (FP32 in the
+    // solver), FP64 across threads, blocks and planes
+    TIn acc = 0, acc_r = 0, acc_a = 0;
     const int e0 = mt.rowstart[2 * pb], e1 = mt.rowstart[min(2 * (pb + npair), m)];
 #pragma unroll 4
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -659,18 +660,18 @@ k_rows_inv_masked(MvmGeom g, MaskTables mt, const FrameState* st, const cplx_t<T
         const TIn out = cs * (TIn)v + nv * xi;
         y[vbase + e] = out;
         if (cgm) {
-            acc += (double)xi * (double)out;
-            acc_r += (double)ri * (double)out;
-            acc_a += (double)out * (double)out;
+            acc = fma(xi, out, acc);
+            acc_r = fma((TIn)ri, out, acc_r);
+            acc_a = fma(out, out, acc_a);
         }
     }
     if (cgm) {
         double* dp = cg.dot_part + (((size_t)f * g.NPout + pp) * gridDim.z + blockIdx.z) * 3;
-        const double s0 = block_sum<T>(acc, red);
+        const double s0 = block_sum<T>((double)acc, red);
         if (threadIdx.x == 0) dp[0] = s0;
-        const double s1 = block_sum<T>(acc_r, red);
+        const double s1 = block_sum<T>((double)acc_r, red);
         if (threadIdx.x == 0) dp[1] = s1;
-        const double s2 = block_sum<T>(acc_a, red);
+        const double s2 = block_sum<T>((double)acc_a, red);
         if (threadIdx.x == 0) dp[2] = s2;
     }
 }
@@ -681,6 +682,14 @@ cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables&
                             TIn* y, const CgVecs* cg, const cplx_t<T>* tw, int rg) {
     const CgVecs cgv = cg ? *cg : CgVecs{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     if (rg != 1 && rg != row_groups(g.m)) return cudaErrorInvalidValue;
+    if constexpr (std::is_same<T, float>::value && std::is_same<TIn, float>::value) {
+        if (rg == 1) {
+            bool used = false;
+            const cudaError_t e =
+                rows_inv_pp(L, g, mt, B, st, Y1T, xin, noise_var, fscale, y, cg, tw, g_max_smem, &used);
+            if (e != cudaSuccess || used) return e;
+        }
+    }
     const size_t smem = rows_smem<T>(g, rg == 1 ? g.m : 2 * kRowPairsPerBlock);
     if (smem > (size_t)g_max_smem) return cudaErrorInvalidValue;
 #define TOMO_L(PC)                                                                                \
@@ -1510,6 +1519,7 @@ cudaError_t init_kernel_attributes() {
     if ((e = allow_smem(k_setup_rows, dyn)) != cudaSuccess) return e;
     if ((e = allow_smem(k_setup_cols, dyn)) != cudaSuccess) return e;
     if ((e = init_fft_constants()) != cudaSuccess) return e;
+    if ((e = init_rows_pp_attributes(dyn)) != cudaSuccess) return e;
     g_max_smem = dyn;
     return cudaSuccess;
 }

@@ -122,6 +122,20 @@ cudaError_t rows_inv_masked(const Launch& L, const MvmGeom& g, const MaskTables&
                             const double* noise_var, const double2* fscale, TIn* y, const CgVecs* cg,
                             const cplx_t<T>* tw, int rg = 1);
 
+// Persistent, prefetching forms of the FP32 row passes (rows_pp.cu), used by
+// rows_fwd / rows_inv_masked when they apply (fused FFT size, whole planes per
+// block, 16-byte aligned slices, n_vs a multiple of 4; row-forward in plain or
+// CG mode); *used reports whether they ran.
+cudaError_t rows_inv_pp(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const FrameState* st,
+                        const float2* Y1T, const float* xin, const double* noise_var, const double2* fscale,
+                        float* y, const CgVecs* cg, const float2* tw, int max_smem, bool* used);
+cudaError_t rows_fwd_pp(const Launch& L, const MvmGeom& g, const MaskTables& mt, int B, const float* x,
+                        const CgVecs* cg, const FrameState* st, float2* X1T, const float2* tw, int max_smem,
+                        bool* used);
+cudaError_t init_rows_pp_attributes(int dyn);
+// Reads and clears the device's flag of bounded waits that expired (0: none).
+cudaError_t take_wait_error(int* flag);
+
 // Row-inverse pass to a dense m x m output per plane: Yd [B][NPout][m][m].
 template <typename T>
 cudaError_t rows_inv_dense(const Launch& L, const MvmGeom& g, int B, const cplx_t<T>* Y1T,

@@ -194,3 +194,16 @@ def test_covariance_scales_as_r0_to_minus_five_thirds(lgs):
     A2 = cov.system_matrix_r0(cfg, 0.1, noise_scale=2.5)
     nv = cov.noise_variance(cfg)
     assert np.allclose(np.diag(A2) - np.diag(cov.css_dense(dict(cfg, r0=0.1))), 2.5 * nv, rtol=1e-13)
+
+
+def test_css_block_is_a_block_of_the_dense_matrix():
+    # the column-restricted form used to time a principal block of the ELT
+    # matrix: the same entries as the dense matrix's rows and columns
+    from conftest import small_cfg
+    cfg = small_cfg(n=6, lgs=True, obstruction=0.2, D=3.0)
+    S = cov.css_dense(cfg)
+    rng = np.random.default_rng(3)
+    rows = rng.choice(S.shape[0], 17, replace=False)
+    cols = rng.choice(S.shape[0], 11, replace=False)
+    assert np.array_equal(cov.css_block(cfg, rows, cols), S[np.ix_(rows, cols)])
+    assert np.array_equal(cov.css_rows(cfg, rows), S[rows])
