@@ -426,6 +426,85 @@ def train_warm_start(tomo, torch, h, cfg, layout, sub, seed, n_train=256, steps=
     return float(np.mean(losses[:5])), float(np.mean(losses[-20:]))
 
 
+def run_learned_flexible(tomo, torch, W, args, stream, flush, cfg, s, F, P, rank, world, n_train=256, hidden=16,
+                         steps=300, B=32):
+    """The learned preconditioner in flexible PCG (plain PCG with M as its
+    fallback) on the bench frames.  The network (input [r, M r], output a
+    correction of M r) is trained offline on (r_k, zeta* - x_k) pairs of
+    truncated PCG solves (k = 0, 8, 30, 80 iterations) of other seeded frames,
+    each pair scaled to |r_k| = 1."""
+    import numpy as np
+    h = tomo.tomo_create(cfg, stream=stream, max_batch=F, precond=True, fft_P=P)
+    try:
+        layout, sub, _ = tomo.tomo_layout(h)
+        full, _ = W.slope_frames_parallel(cfg, n_train, seed=2500 + rank)
+        st = torch.tensor(tomo.valid_slopes(full, sub), dtype=torch.float32, device="cuda").contiguous()
+        t0 = time.perf_counter()
+        rp, ep = [], []
+        for b0 in range(0, n_train, F):
+            nb = min(F, n_train - b0)
+            sb = st[b0:b0 + nb].contiguous()
+            zs = torch.zeros_like(sb)
+            tomo.tomo_solve(h, sb, nb, tomo.solve_opts(tol=1e-6, max_iter=30000, max_refine=3, precond=True), zs)
+            for k in (0, 8, 30, 80):
+                x = torch.zeros_like(sb)
+                if k:
+                    tomo.tomo_solve(h, sb, nb, tomo.solve_opts(tol=1e-12, max_iter=k, max_refine=0, check_every=1,
+                                                               precond=True), x)
+                Ax = torch.empty_like(sb)
+                tomo.tomo_apply_css(h, x, Ax, nb)
+                r = sb - Ax
+                nr = r.norm(dim=1, keepdim=True)
+                rp.append(r / nr)
+                ep.append((zs - x) / nr)
+        rp, ep = torch.cat(rp).contiguous(), torch.cat(ep).contiguous()
+        NP = 2 * layout.n_gs
+        tomo.tomo_ws_init(h, hidden=hidden, max_batch=F, in_scale=float(1.0 / rp.std()), out_scale=float(ep.std()),
+                          precond_input=True, pre_gain=1.0)
+        init = W.warm_start_init(NP, hidden, seed=2500 + rank, cin=2 * NP, last_gain=0.0)
+        tomo.tomo_ws_set_params(h, init)
+        rng = np.random.default_rng(2500 + rank)
+        losses = []
+        for step in range(steps):
+            idx = torch.tensor(rng.choice(rp.shape[0], B, replace=False), device="cuda")
+            losses.append(tomo.tomo_ws_train_step(h, rp[idx].contiguous(), ep[idx].contiguous(), B,
+                                                  1e-3 if step < 0.75 * steps else 3e-4))
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        z = torch.zeros_like(s)
+        out = {}
+        for name, pc in (("pcg", True), ("learned", "learned")):
+            opts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=16, precond=pc)
+            tomo.tomo_solve(h, s, F, opts, z)
+            evs, info = [], None
+            for _ in range(max(1, min(args.steps, 2))):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = tomo.tomo_solve(h, s, F, opts, z)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+            out[name] = {"value": world * F / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms,
+                         "iters_mean": float(info["iters"].mean()),
+                         "fallbacks": int((info["status"] == tomo.FRAME_FALLBACK_PLAIN_CG).sum()),
+                         "all_converged": bool(np.isin(info["status"], [0, tomo.FRAME_FALLBACK_PLAIN_CG]).all()
+                                               and (info["relres"] <= TOL).all())}
+        res = out["learned"]
+        res["pcg_same_handle"] = out["pcg"]
+        res["iteration_gain_vs_pcg"] = 1.0 - res["iters_mean"] / out["pcg"]["iters_mean"]
+        res["frames_per_s_gain_vs_pcg"] = res["value"] / out["pcg"]["value"] - 1.0
+        res["training"] = {"pairs": int(rp.shape[0]), "frames": n_train, "steps": steps, "batch": B,
+                           "hidden": hidden, "loss_first": float(np.mean(losses[:5])),
+                           "loss_last": float(np.mean(losses[-20:])), "wall_s": train_s,
+                           "network": f"3x3 CNN [r, M r] {2 * NP}-{hidden}-{hidden}-{hidden}-{NP}, FP32"}
+        return res
+    finally:
+        tomo.tomo_destroy(h)
+
+
 def run_moao(tomo, torch, W, args, stream, flush, F, rank, world):
     """MOAO variant: the elt_moao system (32 targets), F frames in four groups
     generated at r0 = 0.10, 0.133, 0.167, 0.20 m and solved in one batch with
@@ -716,6 +795,7 @@ def run_ours(args):
 
         # the same frames with the block-circulant preconditioner, and with MINRES (reported beside the headline)
         pcg = minres = warm_prev = learned = single = direct = moao = block = learned_block = mixed = None
+        learned_flex = None
         small = []
         if not args.no_variants:
             mixed = run_mixed(tomo, torch, W, args, stream, flush, h, cfg, sub, layout, rank, world, 4 * F)
@@ -829,6 +909,8 @@ def run_ours(args):
                 learned_block = variant(tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, precond=True,
                                                         warm_start=2, method="block"),
                                         note="the same network as warm start of block PCG")
+                learned_flex = run_learned_flexible(tomo, torch, W, args, stream, flush, cfg, s, F, layout.P, rank,
+                                                    world)
         if world == 1 and not args.no_cpu_baseline:
             # the library on the small systems the oracle is timed on end to end (same seeds)
             small = [gpu_small(tomo, torch, W, "ngs8m", F, 500, stream, flush, max(1, min(args.steps, 3))),
@@ -904,7 +986,8 @@ def run_ours(args):
                        "solver": "CG, FP32 vectors/FFTs/spectra, FP64 dots and alpha/beta, FP64 true residual"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "pcg": pcg, "block_pcg": block, "minres": minres, "learned_pcg": learned,
-            "learned_block_pcg": learned_block, "pcg_warm_previous": warm_prev,
+            "learned_block_pcg": learned_block, "learned_flexible_pcg": learned_flex,
+            "pcg_warm_previous": warm_prev,
             "single_frame_pcg": single, "direct_mvm": direct, "moao_32_targets": moao, "mixed_precision": mixed,
             "solve": {"iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                       "relres_max": float(info["relres"].max()), "all_converged": ok,

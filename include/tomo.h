@@ -71,11 +71,14 @@ typedef enum {
 enum {
     TOMO_FRAME_CONVERGED = 0,  /* FP64 true relative residual <= tol           */
     TOMO_FRAME_MAXIT = 1,      /* iteration limit (or opts.deadline_ms) first  */
-    TOMO_FRAME_BREAKDOWN = 2   /* p^T A p <= 0, or a NaN / infinity in the
+    TOMO_FRAME_BREAKDOWN = 2,  /* p^T A p <= 0, or a NaN / infinity in the
                                   frame's slopes, warm start or iterates: the
                                   frame stops and returns its last iterate
                                   (the initial guess when its input is not
                                   finite); the other frames are not affected */
+    TOMO_FRAME_FALLBACK_PLAIN_CG = 3 /* converged, after leaving the flexible
+                                  iteration with the learned preconditioner
+                                  (opts.precond = 2) for PCG with M alone     */
 };
 
 /* One guide star (Sec. 2 intro): direction alpha [rad] and altitude H [m];
@@ -155,7 +158,12 @@ typedef struct {
     int warm_start;        /* 1: zeta_dev holds the initial guess on entry;
                               2: the initial guess is the warm-start network's  */
     int check_every;       /* iterations between host convergence checks (>= 1)   */
-    int precond;           /* 1: preconditioned CG with the block-circulant M     */
+    int precond;           /* 1: preconditioned CG with the block-circulant M;
+                              2: flexible PCG with the learned preconditioner
+                              z = pre_gain M r + out_scale N([r, M r]) (the
+                              warm-start network initialised with
+                              precond_input = 1, see tomo_ws_init), plain PCG
+                              with M as its fallback (method CG only)          */
     int method;            /* TOMO_METHOD_CG (0), _MINRES (1) or _BLOCK (2)        */
     int precision;         /* TOMO_PREC_FP32 (0), _FP64 (1) or _MIXED (2), below   */
     double inner_tol;      /* TOMO_PREC_MIXED: relative residual reduction asked
@@ -166,6 +174,15 @@ typedef struct {
                               frames still iterating stop (TOMO_FRAME_MAXIT),
                               the outputs are written as usual and the call
                               returns TOMO_ETIMEOUT                             */
+    int host_loop;         /* 0 (default): the whole iteration loop of CG, PCG,
+                              MINRES and FP64 CG is one CUDA graph launch with
+                              conditional nodes: check_every iterations, a
+                              device-side convergence and budget check, the FP64
+                              true residual and its restarts, repeated while a
+                              frame is active; the host waits only to read
+                              info_host.  1: the host checks convergence every
+                              check_every iterations.  Block CG always runs its
+                              loop on the host.                                 */
 } tomo_solve_opts;
 
 /* Arithmetic of a solve (tomo_solve_opts.precision).

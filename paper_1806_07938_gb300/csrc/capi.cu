@@ -35,6 +35,14 @@ struct GraphCache {
     long long nodes = 0;
 };
 
+// The device-side solve loop: one graph per (batch, chunk, kind) with a WHILE
+// node around {chunk iterations; loop_check; IF {FP64 true residual}; loop_next}.
+struct LoopGraph {
+    cudaGraphExec_t exec = nullptr;
+    int B = -1, chunk = 0, kind = -1;
+    long long body_nodes = 0, if_nodes = 0;   // kernel launches per body pass / per true residual
+};
+
 // Warm-start network state (see tomo_ws_* in include/tomo.h).
 struct WarmStartNet {
     bool ready = false;
@@ -155,6 +163,14 @@ struct tomo_handle {
     double *rel64 = nullptr, *snorm64 = nullptr;     // per frame: outer relative residual, ||s||^2
     float *rhs32 = nullptr, *d32 = nullptr;          // inner right-hand side and correction
     double2* d_fs_outer = nullptr;                   // per-frame (c_f, nu_f) of the outer operator
+    // device-side loop: its state on the device, a pinned copy read back after
+    // the launch, the right-hand side it recomputes the true residual from
+    double* flex_part = nullptr;                     // flexible PCG partial sums [B][nparts][5]
+    LoopGraph loop;
+    LoopState* d_loop = nullptr;
+    LoopState* h_loop = nullptr;
+    bool loop_pending = false;                       // h_loop holds a launch not yet accounted for
+    float* s_loop = nullptr;
     // wall-clock budget of the current call (tomo_solve_opts.deadline_ms)
     bool has_deadline = false, timed_out = false;
     std::chrono::steady_clock::time_point deadline{};
@@ -369,7 +385,17 @@ tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi
 // One FP64 CG iteration (tomo_solve_f64): the scheduled update and new
 // direction (cg64_update), A p with the FP64 product, the partial sums, and
 // the per-frame scalars.
-enum IterKind { kIterCG = 0, kIterPCG = 1, kIterMINRES = 2, kIterCG64 = 3 };
+//
+// One flexible PCG iteration with the learned preconditioner (flex.cu): z from
+// the network on [r, M r] (M r kept for the fallback), the per-frame
+// convergence test, fallback decisions and beta, the new direction, q = A p,
+// alpha and the update.
+enum IterKind { kIterCG = 0, kIterPCG = 1, kIterMINRES = 2, kIterCG64 = 3, kIterFlex = 4 };
+
+// Iterations without progress after which a flexible-PCG frame falls back to PCG with M.
+constexpr int kFlexWindow = 32;
+
+tomo_status ws_forward(tomo_handle* h, const Launch& L, const float* s, int B, float* zeta);
 
 tomo_status iteration(tomo_handle* h, const Launch& L, int B, int kind, std::vector<std::pair<int, int>>* marks) {
     int last = -1;
@@ -387,6 +413,28 @@ tomo_status iteration(tomo_handle* h, const Launch& L, int B, int kind, std::vec
     // slot encoding: pair (start event * 8 + kernel class, end event)
     const int rg = rg_for(h, B);
     TRY(mark(0));
+    if (kind == kIterFlex) {
+        // z = pre_gain M r + out_scale N([r, M r]) (into z), M r (into w)
+        const WarmStartNet& w = h->ws;
+        for (int b0 = 0; b0 < B; b0 += w.maxB) {
+            const int nb = std::min(w.maxB, B - b0);
+            TRY(ws_forward(h, L, h->r + (size_t)b0 * h->N, nb, h->z + (size_t)b0 * h->N));
+            CK(cudaMemcpyAsync(h->w + (size_t)b0 * h->N, w.zpre, sizeof(float) * nb * h->N, cudaMemcpyDeviceToDevice,
+                               L.stream));
+        }
+        TRY(mark(1));
+        CK(flex_dots(L, B, h->N, h->nparts, h->st, h->r, h->Ap, h->z, h->w, h->flex_part));
+        CK(flex_beta(L, B, h->nparts, h->flex_part, kFlexWindow, h->st));
+        CK(flex_dir(L, B, h->N, h->st, h->z, h->w, h->p));
+        TRY(mark(3));
+        TRY(apply_ss32(h, L, h->p, h->Ap, B, h->st, nullptr, h->d_fscale));
+        TRY(mark(2));
+        CK(flex_pq(L, B, h->N, h->nparts, h->st, h->p, h->Ap, h->flex_part));
+        CK(flex_alpha(L, B, h->nparts, h->flex_part, h->st));
+        CK(flex_update(L, B, h->N, h->st, h->x, h->r, h->p, h->Ap));
+        TRY(mark(3));
+        return TOMO_OK;
+    }
     if (kind == kIterCG64) {
         CK(cg64_update(L, B, h->N, h->nparts, h->st, h->x64, h->r64, h->p64, h->Ap64, h->rr64_part));
         TRY(mark(0));
@@ -988,6 +1036,8 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
 void release(tomo_handle* h) {
     if (!h) return;
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
+    if (h->loop.exec) cudaGraphExecDestroy(h->loop.exec);
+    if (h->h_loop) cudaFreeHost(h->h_loop);
     if (h->work) cudaStreamSynchronize(h->work);
     for (void* p : h->allocs) cudaFree(p);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -1216,6 +1266,179 @@ tomo_status run_iterations(tomo_handle* h, const Launch& L, int B, const tomo_so
     return TOMO_OK;
 }
 
+// The FP64 true residual of the device loop (inside its IF node): reads the
+// right-hand side from the handle's buffer (s_loop, or s64 for FP64 CG) and
+// tol / max_refine from the loop state.
+tomo_status true_res_device(tomo_handle* h, const Launch& L, int B, int kind) {
+    const int ms_len = 2 * h->n_vs;
+    if (kind == kIterCG64) {
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->x64, nullptr, nullptr));
+        TRY(apply_ss64(h, L, h->x64, h->yd, B, h->d_fscale));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, 1, h->d_Qs, nullptr, h->yd, nullptr, nullptr));
+        CK(residual64(L, B, h->N, h->nparts, h->s64, h->yd, h->r64, h->res_part));
+    } else {
+        CK(to_f64(L, (size_t)B * h->N, h->x, h->xd));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->xd, nullptr, nullptr));
+        TRY(apply_ss64(h, L, h->xd, h->yd, B, h->d_fscale));
+        if (h->modes) CK(mode_project<double>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->yd, nullptr, nullptr));
+        CK(true_residual(L, B, h->N, h->nparts, h->s_loop, h->yd, h->r, h->res_part));
+    }
+    CK(true_residual_finalize(L, B, h->nparts, h->res_part, 0.0, 0, h->st, h->d_loop));
+    return TOMO_OK;
+}
+
+// Builds (or reuses) the device-loop graph: WHILE (more) { chunk iterations;
+// loop_check, which sets `need`; IF (need) { FP64 true residual }; loop_next,
+// which sets `more` }.  The body is captured from the same launch code as the
+// host loop; the IF node is spliced in through the capture's dependencies.
+tomo_status build_loop_graph(tomo_handle* h, int B, int chunk, int kind) {
+    LoopGraph& lg = h->loop;
+    if (lg.exec && lg.B == B && lg.chunk == chunk && lg.kind == kind) return TOMO_OK;
+    if (lg.exec) {
+        cudaGraphExecDestroy(lg.exec);
+        lg.exec = nullptr;
+    }
+    const long long before = h->launches;
+    Launch Lc{h->work, &h->launches};
+    cudaGraph_t g = nullptr;
+    tomo_status st = TOMO_OK;
+    bool capturing = false;
+    auto bad = [&](cudaError_t e, const char* what) {
+        std::fprintf(stderr, "tomo: device loop graph: %s failed: %s\n", what, cudaGetErrorString(e));
+        st = TOMO_ECUDA;
+    };
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) { bad(e, "cudaGraphCreate"); return st; }
+    cudaGraphConditionalHandle more{}, need{};
+    cudaGraphNodeParams wp{};
+    cudaGraphNodeParams ip{};
+    cudaGraphNode_t wnode = nullptr, inode = nullptr;
+    long long body_nodes = 0, if_nodes = 0;
+    do {
+        if ((e = cudaGraphConditionalHandleCreate(&more, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) {
+            bad(e, "cudaGraphConditionalHandleCreate");
+            break;
+        }
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = more;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp)) != cudaSuccess) {
+            bad(e, "cudaGraphAddNode (while)");
+            break;
+        }
+        cudaGraph_t body = wp.conditional.phGraph_out[0];
+        if ((e = cudaGraphConditionalHandleCreate(&need, body, 0, 0)) != cudaSuccess) {
+            bad(e, "cudaGraphConditionalHandleCreate");
+            break;
+        }
+        if ((e = cudaStreamBeginCaptureToGraph(h->work, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess) {
+            bad(e, "cudaStreamBeginCaptureToGraph (body)");
+            break;
+        }
+        capturing = true;
+        const long long b0 = h->launches;
+        for (int i = 0; i < chunk && st == TOMO_OK; ++i) st = iteration(h, Lc, B, kind, nullptr);
+        if (st != TOMO_OK) break;
+        if ((e = loop_check(Lc, B, h->st, h->d_loop, need)) != cudaSuccess) { bad(e, "loop_check"); break; }
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        if ((e = cudaStreamGetCaptureInfo(h->work, &cs, nullptr, nullptr, &deps, nullptr, &nd)) != cudaSuccess) {
+            bad(e, "cudaStreamGetCaptureInfo");
+            break;
+        }
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = need;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&inode, body, deps, nullptr, nd, &ip)) != cudaSuccess) {
+            bad(e, "cudaGraphAddNode (if)");
+            break;
+        }
+        if ((e = cudaStreamUpdateCaptureDependencies(h->work, &inode, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess) {
+            bad(e, "cudaStreamUpdateCaptureDependencies");
+            break;
+        }
+        if ((e = loop_next(Lc, B, h->st, h->d_loop, more)) != cudaSuccess) { bad(e, "loop_next"); break; }
+        body_nodes = h->launches - b0;
+        cudaGraph_t out = nullptr;
+        capturing = false;
+        if ((e = cudaStreamEndCapture(h->work, &out)) != cudaSuccess) { bad(e, "cudaStreamEndCapture (body)"); break; }
+        cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(h->work, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess) {
+            bad(e, "cudaStreamBeginCaptureToGraph (if)");
+            break;
+        }
+        capturing = true;
+        const long long i0 = h->launches;
+        st = true_res_device(h, Lc, B, kind);
+        if_nodes = h->launches - i0;
+        capturing = false;
+        if ((e = cudaStreamEndCapture(h->work, &out)) != cudaSuccess) { bad(e, "cudaStreamEndCapture (if)"); break; }
+        if (st != TOMO_OK) break;
+        if ((e = cudaGraphInstantiate(&lg.exec, g, 0)) != cudaSuccess) { bad(e, "cudaGraphInstantiate"); break; }
+    } while (false);
+    if (capturing) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(h->work, &junk);
+        if (junk && junk != g) cudaGraphDestroy(junk);
+        cudaGetLastError();
+    }
+    cudaGraphDestroy(g);
+    h->launches = before;
+    if (st != TOMO_OK || !lg.exec) {
+        lg.exec = nullptr;
+        return st == TOMO_OK ? TOMO_ECUDA : st;
+    }
+    lg.B = B;
+    lg.chunk = chunk;
+    lg.kind = kind;
+    lg.body_nodes = body_nodes;
+    lg.if_nodes = if_nodes;
+    return TOMO_OK;
+}
+
+// The solve loop as one graph launch on the work stream (no host
+// synchronisation); s: the right-hand side the true residual uses (copied to
+// the handle's buffer; unused for FP64 CG, whose right-hand side is s64).
+tomo_status run_device_loop(tomo_handle* h, const Launch& L, int B, const tomo_solve_opts& o, int kind,
+                            const float* s) {
+    if (!h->d_loop) {
+        TRY(dalloc(h, &h->d_loop, 1));
+        TRY(dalloc(h, &h->s_loop, (size_t)h->max_batch * h->N));
+        CK(cudaMallocHost(&h->h_loop, sizeof(LoopState)));
+    }
+    const int chunk = std::max(1, o.check_every);
+    if (kind != kIterCG64) CK(cudaMemcpyAsync(h->s_loop, s, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
+    unsigned long long budget = 0;
+    if (h->has_deadline) {
+        const double ns =
+            std::chrono::duration<double, std::nano>(h->deadline - std::chrono::steady_clock::now()).count();
+        budget = (unsigned long long)std::max(1.0, ns);
+    }
+    TRY(build_loop_graph(h, B, chunk, kind));
+    CK(loop_start(L, h->d_loop, o.max_iter, budget, o.tol, o.max_refine, chunk));
+    CK(cudaGraphLaunch(h->loop.exec, h->work));
+    CK(cudaMemcpyAsync(h->h_loop, h->d_loop, sizeof(LoopState), cudaMemcpyDeviceToHost, h->work));
+    h->loop_pending = true;
+    return TOMO_OK;
+}
+
+// After the work stream has been synchronised: the device loop's outcome
+// (time budget, launch count: body passes and true residuals).
+void account_loop(tomo_handle* h) {
+    if (!h->loop_pending) return;
+    h->loop_pending = false;
+    const LoopState& ls = *h->h_loop;
+    if (ls.timed_out) h->timed_out = true;
+    const long long passes = ls.chunk > 0 ? ls.iters / ls.chunk : 0;
+    h->launches += passes * h->loop.body_nodes + (long long)ls.true_res_runs * h->loop.if_nodes;
+}
+
 tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_opts& o, float* zeta, float* phase,
                         tomo_frame_info* info, const double* c_scale = nullptr, const double* nu_scale = nullptr,
                         const double* prop_c = nullptr) {
@@ -1276,7 +1499,16 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
     }
     CK(cg_init_scalars(L, B, h->nparts, h->init_part, o.tol, o.warm_start, h->st));
     const bool pcg = o.precond && h->d_M32;
-    const int kind = o.method == TOMO_METHOD_MINRES ? kIterMINRES : (pcg ? kIterPCG : kIterCG);
+    const int kind = o.method == TOMO_METHOD_MINRES ? kIterMINRES
+                     : o.precond == 2                ? kIterFlex
+                     : (pcg ? kIterPCG : kIterCG);
+    if (kind == kIterFlex) {
+        // the learned preconditioner needs the network in its [r, M r] form and
+        // M itself; it is not rescaled per frame (no tomo_solve_r0) nor projected
+        if (!h->ws.ready || !h->ws.hybrid || !h->d_M32 || h->modes || c_scale || nu_scale) return TOMO_EINVAL;
+        if (!h->flex_part) TRY(dalloc(h, &h->flex_part, (size_t)h->max_batch * h->nparts * 5));
+        TRY(ws_layouts(h, L));     // the network's weight layouts, before any graph captures their use
+    }
     if (kind != kIterCG) {
         // the first row-forward pass reads these with zero coefficients
         CK(cudaMemsetAsync(h->z, 0, sizeof(float) * B * h->N, h->work));
@@ -1445,7 +1677,10 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             done = *h->h_nactive == 0;
         }
     }
-    if (block_iters < 0) TRY(run_iterations(h, L, B, o, kind, true_res));
+    if (block_iters < 0) {
+        if (!o.host_loop && !h->timing) TRY(run_device_loop(h, L, B, o, kind, s));
+        else TRY(run_iterations(h, L, B, o, kind, true_res));
+    }
     if (h->modes) CK(mode_project<float>(L, B, ms_len, h->n_gs, h->rg, h->d_Qs, nullptr, h->x, nullptr, nullptr));
     if (prop_c) CK(scale_rows(L, B, h->N, h->d_rhs_scale, h->x, zeta));
     else CK(cudaMemcpyAsync(zeta, h->x, sizeof(float) * B * h->N, cudaMemcpyDeviceToDevice, h->work));
@@ -1460,13 +1695,16 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         std::vector<FrameState> tmp(B);
         CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
         CK(cudaStreamSynchronize(h->work));
+        account_loop(h);
         TRY(check_wait_error());
         for (int f = 0; f < B; ++f) {
             if (block_iters >= 0) tmp[f].iters = (int)block_iters;
             h->frame_iters += tmp[f].iters;
             info[f].iters = tmp[f].iters;
             info[f].refinements = tmp[f].refinements;
-            info[f].status = tmp[f].status;
+            info[f].status = (kind == kIterFlex && tmp[f].fb && tmp[f].status == TOMO_FRAME_CONVERGED)
+                                 ? TOMO_FRAME_FALLBACK_PLAIN_CG
+                                 : tmp[f].status;
             info[f].pad_ = 0;
             info[f].relres = tmp[f].relres;
         }
@@ -1480,6 +1718,7 @@ tomo_status report(tomo_handle* h, int B, tomo_frame_info* info) {
     std::vector<FrameState> tmp(B);
     CK(cudaMemcpyAsync(tmp.data(), h->st, sizeof(FrameState) * B, cudaMemcpyDeviceToHost, h->work));
     CK(cudaStreamSynchronize(h->work));
+    account_loop(h);
     TRY(check_wait_error());
     for (int f = 0; f < B; ++f) {
         h->frame_iters += tmp[f].iters;
@@ -1526,7 +1765,8 @@ tomo_status solve_chunk_f64(tomo_handle* h, const double* s64, int B, const tomo
         CK(true_residual_finalize(L, B, h->nparts, h->res_part, o.tol, max_refine, h->st));
         return TOMO_OK;
     };
-    TRY(run_iterations(h, L, B, o, kIterCG64, true_res));
+    if (!o.host_loop && !h->timing) TRY(run_device_loop(h, L, B, o, kIterCG64, nullptr));
+    else TRY(run_iterations(h, L, B, o, kIterCG64, true_res));
     CK(cudaMemcpyAsync(zeta64, h->x64, sizeof(double) * BN, cudaMemcpyDeviceToDevice, h->work));
     CK(cudaEventRecord(h->ev_out, h->work));
     CK(cudaStreamWaitEvent(h->stream, h->ev_out, 0));
@@ -1659,9 +1899,11 @@ tomo_status check_opts(const tomo_solve_opts& o, int max_batch = 0) {
     if (o.precision != TOMO_PREC_FP32 && o.precision != TOMO_PREC_FP64 && o.precision != TOMO_PREC_MIXED)
         return TOMO_EINVAL;
     if (!(o.inner_tol >= 0) || !(o.inner_tol < 1) || !(o.deadline_ms >= 0)) return TOMO_EINVAL;
+    if (o.host_loop != 0 && o.host_loop != 1) return TOMO_EINVAL;
     if (o.method != TOMO_METHOD_CG && o.method != TOMO_METHOD_MINRES && o.method != TOMO_METHOD_BLOCK)
         return TOMO_EINVAL;
     if (o.method == TOMO_METHOD_MINRES && o.precond) return TOMO_EINVAL;
+    if (o.precond < 0 || o.precond > 2 || (o.precond == 2 && o.method != TOMO_METHOD_CG)) return TOMO_EINVAL;
     if (o.warm_start < 0 || o.warm_start > 2) return TOMO_EINVAL;
     if (o.method == TOMO_METHOD_BLOCK && max_batch > 64) return TOMO_EINVAL;
     return TOMO_OK;
@@ -1679,6 +1921,7 @@ tomo_solve_opts default_opts() {
     o.precision = TOMO_PREC_FP32;
     o.inner_tol = 0.0;
     o.deadline_ms = 0.0;
+    o.host_loop = 0;
     return o;
 }
 

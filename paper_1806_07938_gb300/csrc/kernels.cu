@@ -817,6 +817,9 @@ __global__ void k_cg_init_scalars(int B, int nparts, const double* __restrict__ 
     s.fresh = 1;
     s.pad_ = 0;
     s.delta = 0.0;
+    s.fb = 0;
+    s.ckpt_iter = 0;
+    s.rr_ckpt = rr;
     st[f] = s;
 }
 
@@ -1045,9 +1048,13 @@ cudaError_t true_residual(const Launch& L, int B, int N, int nparts, const float
 }
 
 __global__ void k_true_residual_finalize(int B, int nparts, const double* __restrict__ parts, double tol,
-                                         int max_refine, FrameState* st) {
+                                         int max_refine, FrameState* st, const LoopState* __restrict__ ls) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= B) return;
+    if (ls) {
+        tol = ls->tol;
+        max_refine = ls->stop ? 0 : ls->max_refine;
+    }
     FrameState s = st[f];
     if (s.snorm2 <= 0.0) { s.relres = 0.0; s.status = 0; s.active = 0; st[f] = s; return; }
     double rr = 0.0;
@@ -1075,8 +1082,87 @@ __global__ void k_true_residual_finalize(int B, int nparts, const double* __rest
 }
 
 cudaError_t true_residual_finalize(const Launch& L, int B, int nparts, const double* parts, double tol, int max_refine,
-                                   FrameState* st) {
-    k_true_residual_finalize<<<(B + 127) / 128, 128, 0, L.stream>>>(B, nparts, parts, tol, max_refine, st);
+                                   FrameState* st, const LoopState* ls) {
+    k_true_residual_finalize<<<(B + 127) / 128, 128, 0, L.stream>>>(B, nparts, parts, tol, max_refine, st, ls);
+    count(L);
+    return cudaGetLastError();
+}
+
+// --- device-side loop control (conditional graph nodes) ---------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void k_loop_start(LoopState* ls, long long max_iter, unsigned long long budget, double tol, int max_refine,
+                             int chunk) {
+    ls->iters = 0;
+    ls->max_iter = max_iter;
+    ls->budget = budget;
+    ls->tol = tol;
+    ls->max_refine = max_refine;
+    ls->chunk = chunk;
+    ls->stop = 0;
+    ls->timed_out = 0;
+    ls->true_res_runs = 0;
+    ls->t0 = global_ns();
+}
+
+cudaError_t loop_start(const Launch& L, LoopState* ls, long long max_iter, unsigned long long budget_ns, double tol,
+                       int max_refine, int chunk) {
+    k_loop_start<<<1, 1, 0, L.stream>>>(ls, max_iter, budget_ns, tol, max_refine, chunk);
+    count(L);
+    return cudaGetLastError();
+}
+
+__global__ void k_loop_check(int B, FrameState* st, LoopState* ls, cudaGraphConditionalHandle need) {
+    __shared__ int active, stop;
+    if (threadIdx.x == 0) {
+        active = 0;
+        ls->iters += ls->chunk;
+        const bool late = ls->budget != 0 && global_ns() - ls->t0 > ls->budget;
+        if (late) ls->timed_out = 1;
+        stop = (ls->iters >= ls->max_iter || late) ? 1 : 0;
+        if (stop) ls->stop = 1;
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < B; f += blockDim.x) {
+        if (!st[f].active) continue;
+        if (stop) {
+            st[f].active = 0;
+            st[f].status = 1;  // TOMO_FRAME_MAXIT
+        } else {
+            atomicAdd(&active, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool run = active == 0 || stop;
+        if (run) ls->true_res_runs += 1;
+        cudaGraphSetConditional(need, run ? 1u : 0u);
+    }
+}
+
+cudaError_t loop_check(const Launch& L, int B, FrameState* st, LoopState* ls, cudaGraphConditionalHandle need) {
+    k_loop_check<<<1, 256, 0, L.stream>>>(B, st, ls, need);
+    count(L);
+    return cudaGetLastError();
+}
+
+__global__ void k_loop_next(int B, const FrameState* st, const LoopState* ls, cudaGraphConditionalHandle more) {
+    __shared__ int active;
+    if (threadIdx.x == 0) active = 0;
+    __syncthreads();
+    for (int f = threadIdx.x; f < B; f += blockDim.x)
+        if (st[f].active) atomicAdd(&active, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(more, (active > 0 && !ls->stop) ? 1u : 0u);
+}
+
+cudaError_t loop_next(const Launch& L, int B, const FrameState* st, const LoopState* ls,
+                      cudaGraphConditionalHandle more) {
+    k_loop_next<<<1, 256, 0, L.stream>>>(B, st, ls, more);
     count(L);
     return cudaGetLastError();
 }

@@ -46,9 +46,13 @@ struct FrameState {
     int status;      // TOMO_FRAME_*
     int refinements; // restarts from the true residual
     double gamma;    // PCG: r^T M^{-1} r of the previous iteration; MINRES: r^T A r
-    int fresh;       // PCG, MINRES: 1 on the first iteration after a (re)start
+    int fresh;       // PCG, MINRES, flexible PCG: 1 on the first iteration after a (re)start
     int pad_;
     double delta;    // MINRES: (Ap)^T (Ap) of the current direction
+    // flexible (learned) PCG
+    int fb;          // 1 once the frame has fallen back to PCG with M alone
+    int ckpt_iter;   // iteration of the last progress checkpoint
+    double rr_ckpt;  // r^T r at that checkpoint
 };
 
 // Masked-vector index tables: valid entries of row r are [rowstart[r], rowstart[r+1]),
@@ -164,14 +168,56 @@ cudaError_t pcg_scalars(const Launch& L, int B, int NP, const double* rr_part, c
 // alpha = rho / (Ap)^T(Ap); the convergence test uses r^T r of the row-forward pass.
 cudaError_t mr_scalars(const Launch& L, int B, int NP, const double* rr_part, const double* dot_part,
                        FrameState* st);
+// State of a solve's device-side loop (a CUDA graph with conditional nodes:
+// WHILE {check_every iterations; loop_check; IF {true residual}; loop_next}).
+struct LoopState {
+    long long iters;            // iterations run in this solve (in chunks of `chunk`)
+    long long max_iter;
+    unsigned long long t0;      // GPU global timer at the start of the loop [ns]
+    unsigned long long budget;  // time budget [ns] (0: none)
+    double tol;
+    int max_refine;
+    int chunk;
+    int stop;                   // the iteration or time budget is spent: the next true residual is final
+    int timed_out;              // the time budget ran out
+    int true_res_runs;          // true residuals computed (IF node bodies run)
+};
+// Initialises the loop state of a solve (before the graph launch).
+cudaError_t loop_start(const Launch& L, LoopState* ls, long long max_iter, unsigned long long budget_ns, double tol,
+                       int max_refine, int chunk);
+// Adds a chunk to the iteration count, stops the active frames (TOMO_FRAME_MAXIT)
+// once a budget is spent, and sets `need_true_res` to 1 when no frame is
+// active or the budget is spent.
+cudaError_t loop_check(const Launch& L, int B, FrameState* st, LoopState* ls, cudaGraphConditionalHandle need_true_res);
+// Sets `more` to 1 while a frame is active (after the true residual's restarts).
+cudaError_t loop_next(const Launch& L, int B, const FrameState* st, const LoopState* ls,
+                      cudaGraphConditionalHandle more);
 cudaError_t to_f64(const Launch& L, size_t n, const float* a, double* b);
 cudaError_t true_residual(const Launch& L, int B, int N, int nparts, const float* s,
                           const double* Ax, float* r, double* parts);
+// With ls (device loop), tol and max_refine are read from it (max_refine 0 once ls->stop is set).
 cudaError_t true_residual_finalize(const Launch& L, int B, int nparts, const double* parts,
-                                   double tol, int max_refine, FrameState* st);
+                                   double tol, int max_refine, FrameState* st, const LoopState* ls = nullptr);
 cudaError_t count_active(const Launch& L, int B, const FrameState* st, int* n_active);
 // v [B][N]: frames with status TOMO_FRAME_BREAKDOWN set to zero.
 cudaError_t zero_broken(const Launch& L, int B, int N, const FrameState* st, float* v);
+
+// --- flexible (learned) PCG (flex.cu) ----------------------------------------------
+// Vectors [B][N] FP32; partial sums [B][nparts][5] / [B][nparts].
+// flex_dots: r^T r, r^T zN, q^T zN, r^T zM, q^T zM (q = A p of the previous direction).
+cudaError_t flex_dots(const Launch& L, int B, int N, int nparts, const FrameState* st, const float* r, const float* q,
+                      const float* zN, const float* zM, double* parts);
+// Convergence test, fallback decisions, beta (Polak-Ribiere in the form -alpha q^T z / r_old^T z_old).
+cudaError_t flex_beta(const Launch& L, int B, int nparts, const double* parts, int window, FrameState* st);
+// p = z + beta p with z = zM (fallen back) or zN (flexible), active frames.
+cudaError_t flex_dir(const Launch& L, int B, int N, const FrameState* st, const float* zN, const float* zM, float* p);
+cudaError_t flex_pq(const Launch& L, int B, int N, int nparts, const FrameState* st, const float* p, const float* q,
+                    double* parts);
+// alpha = r^T z / p^T q (breakdown when p^T q <= 0 or not finite); iters += 1.
+cudaError_t flex_alpha(const Launch& L, int B, int nparts, const double* parts, FrameState* st);
+// x += alpha p, r -= alpha q, active frames.
+cudaError_t flex_update(const Launch& L, int B, int N, const FrameState* st, float* x, float* r, const float* p,
+                        const float* q);
 
 // --- FP64 solves and mixed-precision refinement (solve64.cu) --------------------
 // FP64 CG vectors [B][N]; partial sums [B][nparts] (r^T r, s^T s: [B][2][nparts]

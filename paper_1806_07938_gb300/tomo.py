@@ -15,7 +15,7 @@ import numpy as np
 from . import _build
 
 TOMO_OK, TOMO_EINVAL, TOMO_ENOMEM, TOMO_ECUDA, TOMO_ETIMEOUT, TOMO_ERANGE = range(6)
-FRAME_CONVERGED, FRAME_MAXIT, FRAME_BREAKDOWN = range(3)
+FRAME_CONVERGED, FRAME_MAXIT, FRAME_BREAKDOWN, FRAME_FALLBACK_PLAIN_CG = range(4)
 PRECISIONS = {"fp32": 0, "fp64": 1, "mixed": 2}
 
 
@@ -46,7 +46,7 @@ class tomo_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("check_every", ctypes.c_int), ("precond", ctypes.c_int),
                 ("method", ctypes.c_int), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("deadline_ms", ctypes.c_double)]
+                ("deadline_ms", ctypes.c_double), ("host_loop", ctypes.c_int)]
 
 
 class tomo_frame_info(ctypes.Structure):
@@ -237,14 +237,19 @@ SLOPE_MODELS = {"hudgin": 0, "fried": 1}
 
 
 def solve_opts(tol=1e-4, max_iter=10000, max_refine=2, warm_start=0, check_every=32, precond=False, method="cg",
-               precision="fp32", inner_tol=0.0, deadline_ms=0.0):
+               precision="fp32", inner_tol=0.0, deadline_ms=0.0, host_loop=False):
     """warm_start: 0 cold, 1 zeta holds the guess, 2 the warm-start network's guess;
+    precond: False / True (block-circulant M) or "learned" (flexible PCG with the
+    network's correction of M r, plain PCG as fallback);
     method: "cg", "minres" or "block" (block CG over the frames of a chunk);
     precision: "fp32", "fp64" (tomo_solve_f64 only) or "mixed" (FP64 outer
     refinement around FP32 inner solves to inner_tol, 0 = automatic);
-    deadline_ms > 0: the call's wall-clock budget (TOMO_ETIMEOUT when spent)."""
-    return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every, int(bool(precond)),
-                           METHODS[method], PRECISIONS[precision], float(inner_tol), float(deadline_ms))
+    deadline_ms > 0: the call's wall-clock budget (TOMO_ETIMEOUT when spent);
+    host_loop: convergence checks on the host instead of the single graph launch."""
+    precond = 2 if precond == "learned" else int(precond)
+    return tomo_solve_opts(tol, max_iter, max_refine, int(warm_start), check_every, precond,
+                           METHODS[method], PRECISIONS[precision], float(inner_tol), float(deadline_ms),
+                           int(bool(host_loop)))
 
 
 def tomo_solve(h, slopes, batch, opts, zeta, phase=None):

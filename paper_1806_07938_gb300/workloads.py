@@ -306,11 +306,13 @@ def elongated_noise(cfg, sigma, k=2.0):
     return out
 
 
-def warm_start_init(n_planes, hidden, seed, last_gain=0.1):
+def warm_start_init(n_planes, hidden, seed, last_gain=0.1, cin=None):
     """Seeded He-normal initial parameters of the warm-start network (flat FP32,
-    per layer W [Cout][Cin][3][3] then b [Cout]); the last layer scaled by last_gain."""
+    per layer W [Cout][Cin][3][3] then b [Cout]); the last layer scaled by
+    last_gain; cin: input channels when they differ from n_planes (the
+    network on [r, M r] has 2 n_planes)."""
     rng = np.random.default_rng(seed)
-    ch = [n_planes, hidden, hidden, hidden, n_planes]
+    ch = [n_planes if cin is None else cin, hidden, hidden, hidden, n_planes]
     out = []
     for l in range(4):
         co, ci = ch[l + 1], ch[l]

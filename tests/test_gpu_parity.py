@@ -707,3 +707,57 @@ def test_deadline_returns_etimeout(T):
             T.tomo_solve_f64(H.h, sd, 4, T.solve_opts(tol=1e-10, precision="mixed", deadline_ms=1e-3),
                              torch.zeros_like(sd))
         assert e.value.status == T.TOMO_ETIMEOUT and (e.value.info["status"] == T.FRAME_MAXIT).all()
+
+
+# --------------------------------------------------------------------------- device-side loop
+@pytest.mark.parametrize("method,pcg", [("cg", False), ("cg", True), ("minres", False)])
+def test_device_loop_matches_host_loop(T, method, pcg):
+    # the whole iteration loop as one graph launch (conditional nodes: the
+    # convergence check and the FP64 true residual run on the device) takes
+    # the same steps as the host loop: the same iterates, counts and residuals
+    g = golden("lgs_mid")
+    with Handle(T, g["cfg"], max_batch=4, precond=pcg) as H:
+        zh, ph, ih = H.solve(g["s"], tol=1e-5, max_iter=20000, max_refine=3, precond=pcg, method=method,
+                             check_every=8, host_loop=True)
+        zd, pd, idv = H.solve(g["s"], tol=1e-5, max_iter=20000, max_refine=3, precond=pcg, method=method,
+                              check_every=8)
+        print(method, pcg, "host", ih, "device", idv)
+        assert np.array_equal(ih, idv)
+        assert np.array_equal(zh, zd) and np.array_equal(ph, pd)
+        assert (idv["status"] == 0).all() and (idv["relres"] <= 1e-5).all()
+        # asynchronous: no per-frame info requested, no host wait inside the call
+        sd = dev(g["s"])
+        za = torch.zeros_like(sd)
+        n0 = T.tomo_launch_count(H.h)
+        st = T.lib().tomo_solve(H.h, T._dptr(sd, torch.float32), 4,
+                                T.ctypes.byref(T.solve_opts(tol=1e-5, max_iter=20000, max_refine=3, precond=pcg,
+                                                            method=method, check_every=8)),
+                                T._dptr(za, torch.float32), None, None)
+        assert st == T.TOMO_OK
+        torch.cuda.synchronize()
+        assert np.array_equal(za.double().cpu().numpy(), zd)
+        assert T.tomo_launch_count(H.h) > n0
+
+
+def test_device_loop_restart_and_fp64(T):
+    # a restart from the FP64 true residual inside the graph (the warm start
+    # of test_fp64_restart_fires), and FP64 CG on the device loop
+    g = golden("lgs_mid")
+    with Handle(T, g["cfg"], max_batch=4) as H:
+        x0 = 1e4 * np.random.default_rng(4).standard_normal(g["s"].shape) * np.abs(g["zeta"]).max()
+        infos = []
+        for host in (True, False):
+            zd = dev(x0)
+            infos.append(T.tomo_solve(H.h, dev(g["s"]), 4, T.solve_opts(tol=1e-5, max_iter=40000, max_refine=6,
+                                                                         warm_start=1, check_every=4,
+                                                                         host_loop=host), zd))
+        assert np.array_equal(infos[0], infos[1]) and (infos[1]["refinements"] >= 1).all()
+        sd = dev(g["s"], torch.float64)
+        z = []
+        for host in (True, False):
+            zd = torch.zeros_like(sd)
+            infos.append(T.tomo_solve_f64(H.h, sd, 4, T.solve_opts(tol=1e-10, max_iter=20000, precision="fp64",
+                                                                   host_loop=host), zd))
+            z.append(zd.cpu().numpy())
+        assert np.array_equal(infos[2], infos[3]) and np.array_equal(z[0], z[1])
+        assert (infos[3]["status"] == 0).all() and (infos[3]["relres"] <= 1e-10).all()

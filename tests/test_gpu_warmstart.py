@@ -143,3 +143,136 @@ def test_training_gains_iterations(T):
         assert warm["iters"].mean() < cold["iters"].mean()
     finally:
         T.tomo_destroy(h)
+
+
+# --------------------------------------------------------------------------- learned flexible PCG
+def _lgs_mid_frames(T, n, seed):
+    from paper_1806_07938_gb300 import workloads as W
+    cfg = W.config("lgs_mid")
+    full, sigma = W.slope_frames(cfg, n, seed=seed)
+    cfg["noise_sigma"] = [float(x) for x in sigma]
+    mask = geo.subaperture_mask(cfg["n"], cfg["obstruction"])
+    return cfg, full[..., mask].reshape(n, -1).astype(np.float32)
+
+
+def _bound_ok(cfg, s, z, info):
+    from oracle import covariance as cov
+    from oracle import solve
+    A = cov.system_matrix(cfg)
+    zs = solve.solve_cholesky(A, s.astype(np.float64).T).T
+    bound = info["relres"] * np.linalg.norm(s, axis=1) / min(cfg["noise_sigma"]) ** 2
+    return (np.linalg.norm(z - zs, axis=1) <= bound).all()
+
+
+def test_flexible_pcg_zero_network_is_pcg_and_bad_network_falls_back(T):
+    # with a zero network the learned preconditioner is M itself: flexible
+    # PCG then takes PCG's steps (the Polak-Ribiere beta equals the standard
+    # one for a fixed M in exact arithmetic); a network whose output is no
+    # descent direction makes every frame fall back to PCG with M, which still
+    # converges to the oracle's solution (TOMO_FRAME_FALLBACK_PLAIN_CG)
+    cfg, s = _lgs_mid_frames(T, 4, seed=40)
+    B = 4
+    h = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=B, precond=True)
+    try:
+        sd = torch.tensor(s, device="cuda")
+        zp = torch.zeros_like(sd)
+        pcg = T.tomo_solve(h, sd, B, T.solve_opts(tol=1e-5, max_iter=20000, max_refine=3, precond=True), zp)
+        T.tomo_ws_init(h, hidden=8, max_batch=B, in_scale=1.0, out_scale=1.0, precond_input=True, pre_gain=1.0)
+        zf = torch.zeros_like(sd)
+        flex = T.tomo_solve(h, sd, B, T.solve_opts(tol=1e-5, max_iter=20000, max_refine=3, precond="learned"), zf)
+        print("PCG", pcg["iters"], "flexible, zero network", flex["iters"], flex["status"])
+        assert (flex["status"] == T.FRAME_CONVERGED).all() and (flex["relres"] <= 1e-5).all()
+        assert np.abs(flex["iters"] - pcg["iters"]).max() <= 0.05 * pcg["iters"].max() + 2
+        assert _bound_ok(cfg, s, zf.double().cpu().numpy(), flex)
+        # a harmful network: no M term, large random weights
+        n_par = T.tomo_ws_param_count(h)
+        rng = np.random.default_rng(3)
+        h2 = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=B, precond=True)
+        try:
+            T.tomo_ws_init(h2, hidden=8, max_batch=B, in_scale=1.0, out_scale=1.0, precond_input=True, pre_gain=0.0)
+            T.tomo_ws_set_params(h2, (rng.standard_normal(n_par) * 3.0).astype(np.float32))
+            zb = torch.zeros_like(sd)
+            bad = T.tomo_solve(h2, sd, B, T.solve_opts(tol=1e-5, max_iter=20000, max_refine=3, precond="learned"), zb)
+            print("flexible, harmful network", bad["iters"], bad["status"])
+            assert (bad["status"] == T.FRAME_FALLBACK_PLAIN_CG).all() and (bad["relres"] <= 1e-5).all()
+            assert _bound_ok(cfg, s, zb.double().cpu().numpy(), bad)
+        finally:
+            T.tomo_destroy(h2)
+        # the learned preconditioner needs the [r, M r] network and method CG
+        with pytest.raises(T.TomoError):
+            T.tomo_solve(h, sd, B, T.solve_opts(precond="learned", method="minres"), zf)
+    finally:
+        T.tomo_destroy(h)
+
+
+def residual_pairs(T, h, sd, zstar, B, ks):
+    """(r_k, zeta* - x_k) of truncated PCG solves (x_k after k iterations), each
+    pair scaled to |r_k| = 1: the residuals the preconditioner meets and the
+    errors A^{-1} r_k it should approximate."""
+    rs, es = [], []
+    for k in ks:
+        x = torch.zeros_like(sd)
+        if k > 0:
+            T.tomo_solve(h, sd, B, T.solve_opts(tol=1e-12, max_iter=k, max_refine=0, check_every=1, precond=True), x)
+        Ax = torch.empty_like(sd)
+        T.tomo_apply_css(h, x, Ax, B)
+        r = sd - Ax
+        e = zstar - x
+        nr = r.norm(dim=1, keepdim=True)
+        rs.append(r / nr)
+        es.append(e / nr)
+    return torch.cat(rs).contiguous(), torch.cat(es).contiguous()
+
+
+def test_learned_flexible_pcg_gain(T):
+    # the learned preconditioner trained on (residual, error) pairs of
+    # truncated PCG solves of training frames, then used in flexible PCG on
+    # held-out frames: the gain over PCG with M alone is stated (it may be
+    # negative); every frame converges to the oracle's solution either way
+    cfg, s = _lgs_mid_frames(T, 96, seed=41)
+    n_train, n_test, B = 64, 32, 32
+    h = T.tomo_create(cfg, stream=torch.cuda.current_stream(), max_batch=B, precond=True)
+    try:
+        sd = torch.tensor(s, device="cuda")
+        zs = torch.zeros_like(sd)
+        for b0 in range(0, n_train + n_test, B):
+            T.tomo_solve(h, sd[b0:b0 + B].contiguous(), B, T.solve_opts(tol=1e-6, max_iter=30000, precond=True),
+                         zs[b0:b0 + B])
+        rp, ep = [], []
+        for b0 in range(0, n_train, B):
+            r, e = residual_pairs(T, h, sd[b0:b0 + B].contiguous(), zs[b0:b0 + B].contiguous(), B, (0, 8, 30, 80))
+            rp.append(r)
+            ep.append(e)
+        rp, ep = torch.cat(rp), torch.cat(ep)
+        NP = 2 * len(cfg["gs"])
+        T.tomo_ws_init(h, hidden=16, max_batch=B, in_scale=float(1.0 / rp.std()), out_scale=float(ep.std()),
+                       precond_input=True, pre_gain=1.0)
+        T.tomo_ws_set_params(h, init_params(NP, 16, seed=12, last_gain=0.0, cin=2 * NP))
+        rng = np.random.default_rng(6)
+        losses = []
+        for step in range(400):
+            idx = torch.tensor(rng.choice(rp.shape[0], B, replace=False), device="cuda")
+            losses.append(T.tomo_ws_train_step(h, rp[idx].contiguous(), ep[idx].contiguous(), B,
+                                               1e-3 if step < 300 else 3e-4))
+        st = sd[n_train:].contiguous()
+        out = {}
+        for name, pc in (("pcg", True), ("learned", "learned")):
+            z = torch.zeros_like(st)
+            T.tomo_solve(h, st, n_test, T.solve_opts(tol=1e-4, max_iter=30000, precond=pc), z)   # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = T.tomo_solve(h, st, n_test, T.solve_opts(tol=1e-4, max_iter=30000, precond=pc), z)
+            e1.record()
+            torch.cuda.synchronize()
+            out[name] = (info, e0.elapsed_time(e1), z.double().cpu().numpy())
+        ip, tp, _ = out["pcg"]
+        il, tl, zl = out["learned"]
+        print(f"learned flexible PCG: loss {np.mean(losses[:10]):.3f} -> {np.mean(losses[-50:]):.3f}; "
+              f"iterations PCG {ip['iters'].mean():.1f} learned {il['iters'].mean():.1f} "
+              f"(gain {1 - il['iters'].mean() / ip['iters'].mean():+.1%}); time PCG {tp:.1f} ms learned {tl:.1f} ms "
+              f"(frames/s gain {tp / tl - 1:+.1%}); fallbacks {(il['status'] == T.FRAME_FALLBACK_PLAIN_CG).sum()}")
+        assert np.isin(il["status"], [T.FRAME_CONVERGED, T.FRAME_FALLBACK_PLAIN_CG]).all()
+        assert (il["relres"] <= 1e-4).all()
+        assert _bound_ok(cfg, s[n_train:], zl, il)
+    finally:
+        T.tomo_destroy(h)
