@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--fft-P", type=int, default=-1,
                     help="FFT side of the Sigma_ss product (-1: autotuned; profiling runs pin it, since the "
                          "autotuner's timings are distorted under a profiler)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="for profiling: convergence checks on the host instead of the single graph launch with "
+                         "conditional nodes (the same kernels)")
     ap.add_argument("--profile-block", action="store_true",
                     help="for profiling: solve the frames W + K times with block PCG and nothing else, print a "
                          "short JSON line (not a bench result)")
@@ -743,7 +746,7 @@ def run_ours(args):
                               "relres_max": float(binfo["relres"].max())}), flush=True)
             tomo.tomo_destroy(h)
             return
-        opts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=32)
+        opts = tomo.solve_opts(tol=TOL, max_iter=30000, max_refine=3, check_every=32, host_loop=args.host_loop)
         for _ in range(args.warmup):
             tomo.tomo_solve(h, s, F, opts, z, phi)
         torch.cuda.synchronize()

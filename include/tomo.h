@@ -163,7 +163,9 @@ typedef struct {
                               z = pre_gain M r + out_scale N([r, M r]) (the
                               warm-start network initialised with
                               precond_input = 1, see tomo_ws_init), plain PCG
-                              with M as its fallback (method CG only)          */
+                              with M as its fallback (method CG only): a frame
+                              falls back when r^T z <= 0 or when r^T r sets no
+                              new minimum for 64 iterations                    */
     int method;            /* TOMO_METHOD_CG (0), _MINRES (1) or _BLOCK (2)        */
     int precision;         /* TOMO_PREC_FP32 (0), _FP64 (1) or _MIXED (2), below   */
     double inner_tol;      /* TOMO_PREC_MIXED: relative residual reduction asked

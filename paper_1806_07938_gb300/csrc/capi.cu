@@ -392,8 +392,9 @@ tomo_status apply_os(tomo_handle* h, const Launch& L, const float* z, float* phi
 // alpha and the update.
 enum IterKind { kIterCG = 0, kIterPCG = 1, kIterMINRES = 2, kIterCG64 = 3, kIterFlex = 4 };
 
-// Iterations without progress after which a flexible-PCG frame falls back to PCG with M.
-constexpr int kFlexWindow = 32;
+// Iterations without a new minimum of r^T r after which a flexible-PCG frame
+// falls back to PCG with M.
+constexpr int kFlexWindow = 64;
 
 tomo_status ws_forward(tomo_handle* h, const Launch& L, const float* s, int B, float* zeta);
 

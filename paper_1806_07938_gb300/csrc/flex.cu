@@ -11,8 +11,8 @@
 // with q = A p (r_k - r_{k-1} = -alpha q), p_k = z_k + beta_k p_{k-1},
 // alpha_k = r_k^T z_k / p_k^T q_k.  Plain PCG with M alone is the fallback
 // and the judge: a frame leaves the flexible iteration for good (restarting
-// its direction from M r) when r^T z <= 0 or when r^T r has not decreased
-// over `window` iterations.  The solver reports such frames as
+// its direction from M r) when r^T z <= 0 or when r^T r has set no new
+// minimum for `window` iterations.  The solver reports such frames as
 // TOMO_FRAME_FALLBACK_PLAIN_CG when they converge.
 //
 // Per-thread sums are FP32 (a few tens of products), FP64 across threads,
@@ -117,13 +117,17 @@ __global__ void k_flex_beta(int B, int nparts, const double* __restrict__ parts,
     if (fresh) {
         s.ckpt_iter = s.iters;
         s.rr_ckpt = rr;
-    } else if (!s.fb && s.iters - s.ckpt_iter >= window) {
-        if (!(rr < s.rr_ckpt)) {       // no progress over the window: leave the flexible iteration
+    } else if (!s.fb) {
+        // rr_ckpt: the smallest r^T r so far; no new minimum within `window`
+        // iterations leaves the flexible iteration (the residual norm of a
+        // working preconditioner is not monotone, but its minimum keeps falling)
+        if (rr < s.rr_ckpt) {
+            s.rr_ckpt = rr;
+            s.ckpt_iter = s.iters;
+        } else if (s.iters - s.ckpt_iter >= window) {
             s.fb = 1;
             fell = true;
         }
-        s.ckpt_iter = s.iters;
-        s.rr_ckpt = rr;
     }
     double rz = v[1], qz = v[2];
     if (!s.fb && (!(rz > 0.0) || !isfinite(rz) || !isfinite(qz))) {

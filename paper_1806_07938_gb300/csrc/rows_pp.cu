@@ -34,16 +34,32 @@ inline void bump(const Launch& L) {
     if (L.counter) ++*L.counter;
 }
 
-__device__ __forceinline__ double bsum(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+// Block sum of FP32 per-thread partials: within each warp in FP32 with an
+// error-free transformation (Knuth's TwoSum: the rounding error of every
+// addition is carried along, so the warp's sum is exact to about FP32
+// precision squared), then the eight warp sums in FP64 by thread 0 (GB300's
+// FP64 rate is ~1/64 of its FP32 rate, so FP64 shuffles cost more than the
+// rest of the reduction).
+__device__ __forceinline__ double bsum32(float v, double* red) {
+    float s = v, c = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float t = __shfl_down_sync(0xffffffffu, s, o);
+        const float tc = __shfl_down_sync(0xffffffffu, c, o);
+        const float u = s + t;
+        const float bp = u - s;
+        const float err = (s - (u - bp)) + (t - bp);
+        s = u;
+        c += tc + err;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
-    if (lane == 0) red[warp] = v;
+    if (lane == 0) red[warp] = (double)s + (double)c;
     __syncthreads();
-    double s = 0.0;
+    double out = 0.0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    return s;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) out += red[w];
+    return out;
 }
 
 // Thread 0 waits for the barrier phase (bounded), the block learns the
@@ -172,11 +188,11 @@ k_rows_inv_pp(MvmGeom g, MaskTables mt, int items, const FrameState* __restrict_
         }
         if (cgm) {
             double* dp = cg.dot_part + (size_t)t * 3;
-            const double s0 = bsum((double)acc, red);
+            const double s0 = bsum32(acc, red);
             if (threadIdx.x == 0) dp[0] = s0;
-            const double s1 = bsum((double)acc_r, red);
+            const double s1 = bsum32(acc_r, red);
             if (threadIdx.x == 0) dp[1] = s1;
-            const double s2 = bsum((double)acc_a, red);
+            const double s2 = bsum32(acc_a, red);
             if (threadIdx.x == 0) dp[2] = s2;
         }
         __syncthreads();                       // F is rebuilt for the next plane
@@ -274,7 +290,7 @@ k_rows_fwd_pp(MvmGeom g, MaskTables mt, int items, const float* __restrict__ x, 
             fft_rounds<PC, C, true, kPPRound>(F + g0 * RS, RS, min(kPPRound, npl - g0), g.plan, tw, nullptr, lane, n,
                                               P);
         if (MODE == 1) {
-            const double s = bsum((double)rr, red);
+            const double s = bsum32(rr, red);
             if (threadIdx.x == 0) cg.rr_part[t] = s;
         }
         __syncthreads();

@@ -166,9 +166,12 @@ def _bound_ok(cfg, s, z, info):
 
 def test_flexible_pcg_zero_network_is_pcg_and_bad_network_falls_back(T):
     # with a zero network the learned preconditioner is M itself: flexible
-    # PCG then takes PCG's steps (the Polak-Ribiere beta equals the standard
-    # one for a fixed M in exact arithmetic); a network whose output is no
-    # descent direction makes every frame fall back to PCG with M, which still
+    # PCG is then PCG with M in its textbook form (Polak-Ribiere beta equals
+    # the standard one for a fixed M in exact arithmetic); it must converge
+    # without falling back and in no more iterations than the library's PCG
+    # (Chronopoulos-Gear form, whose FP32 recurrences cost iterations: 540-593
+    # here against 428-479 measured).  A network whose output is no descent
+    # direction makes every frame fall back to PCG with M, which still
     # converges to the oracle's solution (TOMO_FRAME_FALLBACK_PLAIN_CG)
     cfg, s = _lgs_mid_frames(T, 4, seed=40)
     B = 4
@@ -182,7 +185,7 @@ def test_flexible_pcg_zero_network_is_pcg_and_bad_network_falls_back(T):
         flex = T.tomo_solve(h, sd, B, T.solve_opts(tol=1e-5, max_iter=20000, max_refine=3, precond="learned"), zf)
         print("PCG", pcg["iters"], "flexible, zero network", flex["iters"], flex["status"])
         assert (flex["status"] == T.FRAME_CONVERGED).all() and (flex["relres"] <= 1e-5).all()
-        assert np.abs(flex["iters"] - pcg["iters"]).max() <= 0.05 * pcg["iters"].max() + 2
+        assert (flex["iters"] <= 1.1 * pcg["iters"]).all()
         assert _bound_ok(cfg, s, zf.double().cpu().numpy(), flex)
         # a harmful network: no M term, large random weights
         n_par = T.tomo_ws_param_count(h)
