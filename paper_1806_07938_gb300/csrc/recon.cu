@@ -16,6 +16,7 @@
 // reduction dimension into a fixed number of partial tiles that a second
 // kernel adds in a fixed order (deterministic).
 #include <algorithm>
+#include <cstdint>
 
 #include "kernels.cuh"
 
@@ -373,6 +374,188 @@ inline void count2(const Launch& L) {
     if (L.counter) ++*L.counter;
 }
 
+// --- register-tiled forms (N a multiple of 4, 16-byte aligned rows) ---------------
+// Partial Gram tiles as k_gram_part, with the block's column range walked in
+// sub-chunks of 32 columns: the next sub-chunk is loaded into registers (two
+// float4 per matrix and thread) while the current one is multiplied; the
+// transposed shared-memory tiles use an XOR swizzle of the float4 index (gswz)
+// so that the transposed stores are free of bank conflicts and the reads stay
+// float4;
+// each output's per-sub-chunk FP32 sums (32 products) are accumulated with
+// Knuth's TwoSum (error-free) instead of FP64 additions (GB300's FP64 rate is
+// ~1/64 of its FP32 rate), and converted to FP64 once.
+constexpr int kSub = 32;
+
+// Float4 slot of row group g (rows 4g .. 4g + 3) in column col of a
+// transposed tile: g XOR a key of the column.  The loader of a warp writes,
+// per store, 8 rows x 4 columns 8 apart; the key takes 4 distinct even values
+// mod 8 over those columns, so the 32 stores hit 32 distinct banks.
+__device__ __forceinline__ int gkey(int col) { return (col & 7) ^ ((col >> 3) << 1); }
+__device__ __forceinline__ int gswz(int col, int row) { return (((row >> 2) ^ gkey(col)) << 2) | (row & 3); }
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    const float u = hi + x;
+    const float bp = u - hi;
+    lo += (hi - (u - bp)) + (x - bp);
+    hi = u;
+}
+
+__global__ void __launch_bounds__(256, 2)
+k_gram_part4(int B, int N, const float* __restrict__ U, const float* __restrict__ V, double* __restrict__ part) {
+    __shared__ __align__(16) float Us[2][kSub][kBlockMax];
+    __shared__ __align__(16) float Vs[2][kSub][kBlockMax];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    // this block's column range, in whole sub-chunks
+    const int nsub = (N + kSub - 1) / kSub;
+    const int s0 = (int)((long long)nsub * blockIdx.x / gridDim.x);
+    const int s1 = (int)((long long)nsub * (blockIdx.x + 1) / gridDim.x);
+    // loader: row lr, columns lc .. lc + 7 of a sub-chunk
+    const int lr = threadIdx.x / 4, lc = (threadIdx.x % 4) * 8;
+    float4 ua[2], va[2];
+    auto load = [&](int sc) {
+        const int k = sc * kSub + lc;
+        const bool okr = lr < B;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kk = k + 4 * h;
+            if (okr && kk + 3 < N) {
+                ua[h] = __ldg(reinterpret_cast<const float4*>(U + (size_t)lr * N + kk));
+                va[h] = __ldg(reinterpret_cast<const float4*>(V + (size_t)lr * N + kk));
+            } else {
+                float a[4], b[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    a[c] = okr && kk + c < N ? U[(size_t)lr * N + kk + c] : 0.f;
+                    b[c] = okr && kk + c < N ? V[(size_t)lr * N + kk + c] : 0.f;
+                }
+                ua[h] = make_float4(a[0], a[1], a[2], a[3]);
+                va[h] = make_float4(b[0], b[1], b[2], b[3]);
+            }
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float a[4] = {ua[h].x, ua[h].y, ua[h].z, ua[h].w};
+            const float b[4] = {va[h].x, va[h].y, va[h].z, va[h].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int col = lc + 4 * h + c;
+                Us[buf][col][gswz(col, lr)] = a[c];
+                Vs[buf][col][gswz(col, lr)] = b[c];
+            }
+        }
+    };
+    float hi[4][4] = {}, lo[4][4] = {};
+    if (s0 < s1) {
+        load(s0);
+        store(0);
+    }
+    __syncthreads();
+    for (int sc = s0; sc < s1; ++sc) {
+        const int buf = (sc - s0) & 1;
+        if (sc + 1 < s1) load(sc + 1);
+        float a32[4][4] = {};
+#pragma unroll 8
+        for (int kk = 0; kk < kSub; ++kk) {
+            const float4 av = *reinterpret_cast<const float4*>(&Us[buf][kk][(ty ^ gkey(kk)) << 2]);
+            const float4 bv = *reinterpret_cast<const float4*>(&Vs[buf][kk][(tx ^ gkey(kk)) << 2]);
+            const float a[4] = {av.x, av.y, av.z, av.w};
+            const float b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a32[i][j] = fmaf(a[i], b[j], a32[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) two_sum_acc(hi[i][j], lo[i][j], a32[i][j]);
+        if (sc + 1 < s1) store(buf ^ 1);
+        __syncthreads();
+    }
+    double* out = part + (size_t)blockIdx.x * kBlockMax * kBlockMax;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            out[(ty * 4 + i) * kBlockMax + tx * 4 + j] = (double)hi[i][j] + (double)lo[i][j];
+}
+
+// Y[j][k] = Y0[j][k] + sum_i C[i][j] U[i][k] as a tiled product: a block owns
+// 128 columns k and all 64 j; thread (tk, tj) computes k = 4 tk .. 4 tk + 3 and
+// j = 8 tj .. 8 tj + 7; per i one float4 of U (the warp reads 512 contiguous
+// bytes) and two float4 broadcasts of C feed 32 FMAs.
+constexpr int kCombK = 128;
+
+__global__ void __launch_bounds__(256)
+k_block_combine4(int B, int N, const double* __restrict__ C, double scale, const float* __restrict__ U,
+                 const float* Y0, float* Y) {
+    __shared__ __align__(16) float Us[kBlockMax][kCombK];
+    __shared__ __align__(16) float Cs[kBlockMax][kBlockMax];
+    const int k0 = blockIdx.x * kCombK;
+    for (int t = threadIdx.x; t < kBlockMax * kBlockMax; t += blockDim.x) {
+        const int i = t / kBlockMax, j = t % kBlockMax;
+        Cs[i][j] = (i < B && j < B) ? (float)(scale * C[i * B + j]) : 0.f;
+    }
+    for (int t = threadIdx.x; t < kBlockMax * (kCombK / 4); t += blockDim.x) {
+        const int i = t / (kCombK / 4), c4 = t % (kCombK / 4), k = k0 + 4 * c4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < B) {
+            if (k + 3 < N) {
+                v = __ldg(reinterpret_cast<const float4*>(U + (size_t)i * N + k));
+            } else {
+                float a[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) a[c] = k + c < N ? U[(size_t)i * N + k + c] : 0.f;
+                v = make_float4(a[0], a[1], a[2], a[3]);
+            }
+        }
+        *reinterpret_cast<float4*>(&Us[i][4 * c4]) = v;
+    }
+    __syncthreads();
+    const int tk = threadIdx.x % 32, tj = threadIdx.x / 32;
+    float acc[8][4] = {};
+    const int ib = B < kBlockMax ? B : kBlockMax;
+#pragma unroll 4
+    for (int i = 0; i < ib; ++i) {
+        const float4 u = *reinterpret_cast<const float4*>(&Us[i][4 * tk]);
+        const float4 c0 = *reinterpret_cast<const float4*>(&Cs[i][8 * tj]);
+        const float4 c1 = *reinterpret_cast<const float4*>(&Cs[i][8 * tj + 4]);
+        const float cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        const float uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[jj][q] = fmaf(cc[jj], uu[q], acc[jj][q]);
+    }
+    const int k = k0 + 4 * tk;
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        const int j = 8 * tj + jj;
+        if (j >= B) continue;
+        float o[4] = {acc[jj][0], acc[jj][1], acc[jj][2], acc[jj][3]};
+        if (k + 3 < N) {
+            if (Y0) {
+                const float4 y0 = *reinterpret_cast<const float4*>(Y0 + (size_t)j * N + k);
+                o[0] += y0.x;
+                o[1] += y0.y;
+                o[2] += y0.z;
+                o[3] += y0.w;
+            }
+            *reinterpret_cast<float4*>(Y + (size_t)j * N + k) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+            for (int q = 0; q < 4; ++q)
+                if (k + q < N) Y[(size_t)j * N + k + q] = o[q] + (Y0 ? Y0[(size_t)j * N + k + q] : 0.f);
+        }
+    }
+}
+
+bool tiled_ok(int N, const void* a, const void* b, const void* c) {
+    auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    return (N & 3) == 0 && al(a) && al(b) && al(c);
+}
+
 }  // namespace
 
 constexpr int kGramBlocks = 2 * 152;
@@ -383,7 +566,8 @@ cudaError_t gram(const Launch& L, int B, int N, const float* U, const float* V, 
     if (B < 1 || B > kBlockMax || N < 1) return cudaErrorInvalidValue;
     const int nchunks = (N + kGramChunk - 1) / kGramChunk;
     const int blocks = std::min(kGramBlocks, nchunks);
-    k_gram_part<<<blocks, 256, 0, L.stream>>>(B, N, U, V, part);
+    if (tiled_ok(N, U, V, nullptr)) k_gram_part4<<<blocks, 256, 0, L.stream>>>(B, N, U, V, part);
+    else k_gram_part<<<blocks, 256, 0, L.stream>>>(B, N, U, V, part);
     count2(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -395,6 +579,12 @@ cudaError_t gram(const Launch& L, int B, int N, const float* U, const float* V, 
 cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const float* U, const float* Y0, float* Y,
                           double scale) {
     if (B < 1 || B > kBlockMax) return cudaErrorInvalidValue;
+    if (tiled_ok(N, U, Y0, Y)) {
+        // the tiled form reads Y0 and writes Y per element: they may alias (x += P alpha)
+        k_block_combine4<<<(N + kCombK - 1) / kCombK, 256, 0, L.stream>>>(B, N, C, scale, U, Y0, Y);
+        count2(L);
+        return cudaGetLastError();
+    }
     const int blocks = (N + 127) / 128;
     k_block_combine<<<blocks, 128, 0, L.stream>>>(B, N, C, scale, U, Y0, Y);
     count2(L);
