@@ -597,7 +597,7 @@ tomo_status autotune_side(tomo_handle* h) {
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
-    const size_t nK = (size_t)(h->NP * (h->NP + 1) / 2) * nhmax * Pmax;
+    const size_t nK = herm_packed_elems(Pmax, h->NP);
     const size_t nX = (size_t)B * h->NP * nhmax * n;
     if (cudaMalloc(&x, sizeof(float) * B * h->N) != cudaSuccess || cudaMalloc(&y, sizeof(float) * B * h->N) ||
         cudaMalloc(&X1, sizeof(float2) * nX) || cudaMalloc(&Y1, sizeof(float2) * nX) ||
@@ -872,7 +872,7 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         float2* Kfull = nullptr;
         CK(cudaMalloc(&Kfull, sizeof(float2) * (size_t)npl * (h->P / 2 + 1) * h->P));
         TRY(dalloc(h, &h->d_K64, (size_t)npl * (h->P / 2 + 1) * h->P));
-        TRY(dalloc(h, &h->d_K32, (size_t)(h->NP * (h->NP + 1) / 2) * (h->P / 2 + 1) * h->P));
+        TRY(dalloc(h, &h->d_K32, herm_packed_elems(h->P, h->NP)));
         CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));
         CK(gen_css(L, n, h->P, h->NP, h->d, h->n_layers, d_layers, d_alpha, vk, G, false, h->slope_model));
         CK(spectra(L, h->P, npl, h->NP, h->plan, G, H, h->d_tw64, h->d_K64, Kfull));
@@ -894,7 +894,7 @@ tomo_status create_impl(const tomo_config* c, void* stream, tomo_handle* h) {
         CK(cudaMalloc(&K64, sizeof(double2) * Ksz));
         float2* Mfull = nullptr;
         CK(cudaMalloc(&Mfull, sizeof(float2) * Ksz));
-        TRY(dalloc(h, &h->d_M32, (size_t)(h->NP * (h->NP + 1) / 2) * (h->P / 2 + 1) * h->P));
+        TRY(dalloc(h, &h->d_M32, herm_packed_elems(h->P, h->NP)));
         TRY(dalloc(h, &h->d_zero_var, h->NP));
         CK(cudaMemsetAsync(h->d_zero_var, 0, sizeof(double) * h->NP, h->stream));
         CK(cudaMemsetAsync(G, 0, sizeof(double) * Gsz, h->stream));

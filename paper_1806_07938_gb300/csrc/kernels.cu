@@ -294,78 +294,66 @@ __device__ __forceinline__ void block_mul(C* D, int NPmax, int P, int nf, const 
 }
 
 // Hermitian variant for Sigma_ss (NP x NP blocks with K_qp = conj K_pq): only
-// the upper triangle is stored, [kx][ky][e] with e(p, q) the row-major index of
-// p <= q.  Each round stages its ky range of packed entries in shared memory
-// (one coalesced copy), and thread (ky, p) assembles its row K_p. from it.
+// the upper triangle is stored, entry e(p, q) = herm_index(NP, p, q) for
+// p <= q, with the frequencies ky interleaved in groups of eight:
+// [kx][ky / 8][e][ky % 8] (herm_offset; ky padded to a multiple of 8), so that
+// the eight ky of a warp read one contiguous 64-byte segment per entry.
+//
+// One thread per (ky, frame): it reads its x_q(ky) once, streams the packed
+// entries of K(kx, ky) from global memory (L2; the frames of a ky share them
+// through the same requests), applies each off-diagonal entry twice (K_pq to
+// y_p, conj K_pq to y_q) and writes y back over x.  A thread touches only its
+// own column entries, so the product needs no block barrier until its end.
+// Each y_p is accumulated over q in ascending order.
 __host__ __device__ constexpr int herm_index(int NP, int p, int q) { return p * NP - p * (p - 1) / 2 + (q - p); }
 
-// am: bit fl set for the active frames of the block.  PS and NPM, when
-// non-zero, are the column length and the plane stride known at compile time
-// (the strides of every shared-memory access then fold into the instruction).
+__host__ __device__ inline size_t herm_offset(int NP, int P, int kx, int ky, int e) {
+    const int NE = NP * (NP + 1) / 2;
+    const int P8 = (P + 7) / 8;
+    return (((size_t)kx * P8 + (ky >> 3)) * NE + e) * 8 + (ky & 7);
+}
+
 template <typename C, int NP, int PS, int NPM>
-__device__ __forceinline__ void block_mul_herm(C* D, int NPmax_rt, int P_rt, unsigned am, const C* __restrict__ Kc,
-                                               C* Ks) {
+__device__ __forceinline__ void block_mul_herm(C* D, int NPmax_rt, int P_rt, int nf, unsigned am,
+                                               const C* __restrict__ Kc) {
     using T = decltype(C::x);
-    constexpr int NE = NP * (NP + 1) / 2;
     const int P = PS ? PS : P_rt;
     const int NPmax = PS ? NPM : NPmax_rt;
-    const int kyr = blockDim.x / NP;
-    const int kyl = threadIdx.x / NP, pp = threadIdx.x % NP;
-    // row p of K(ky) from the packed upper triangle: K_pq = Kr[rb + q] for
-    // q >= p, conj(K_qp) = conj(Kr[herm_index(NP, q, 0) + p]) for q < p
-    const int rb = herm_index(NP, pp, 0);
-    for (int ky0 = 0; ky0 < P; ky0 += kyr) {
-        const int nky = min(kyr, P - ky0);
-        {
-            const int cnt = nky * NE;
-            const C* src = Kc + (size_t)ky0 * NE;
-            for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * blockDim.x) {
-                C v[4];
+    const int items = P * nf;
+    for (int w = threadIdx.x; w < items; w += blockDim.x) {
+        const int ky = w / nf, fl = w - ky * nf;
+        if (!((am >> fl) & 1u)) continue;
+        C* col = D + (size_t)fl * NPmax * P + ky;
+        const C* Kr = Kc + herm_offset(NP, P, 0, ky, 0);
+        C x[NP];
+        T yr[NP], yi[NP];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (i0 + u * (int)blockDim.x < cnt) v[u] = __ldg(src + i0 + u * blockDim.x);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (i0 + u * (int)blockDim.x < cnt) Ks[i0 + u * blockDim.x] = v[u];
-            }
+        for (int q = 0; q < NP; ++q) {
+            x[q] = col[q * P];
+            yr[q] = 0;
+            yi[q] = 0;
         }
-        __syncthreads();
-        const int ky = ky0 + kyl;
-        const bool on = kyl < nky;
-        C y[kMaxFramesPerBlock];
-        if (on) {
-            C k[NP];
-            const C* Kr = Ks + kyl * NE;
 #pragma unroll
-            for (int q = 0; q < NP; ++q)
-                k[q] = q >= pp ? Kr[rb + q] : cconj(Kr[herm_index(NP, q, 0) + pp]);
-            const C* col0 = D + ky;
+        for (int p = 0; p < NP; ++p) {
 #pragma unroll
-            for (int fl = 0; fl < kMaxFramesPerBlock; ++fl) {
-                if ((am >> fl) & 1u) {
-                    const C* col = col0 + fl * NPmax * P;
-                    T ar = 0, ai = 0;
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) {
-                        const C x = col[q * P];
-                        ar = fma(k[q].x, x.x, ar);
-                        ar = fma(-k[q].y, x.y, ar);
-                        ai = fma(k[q].x, x.y, ai);
-                        ai = fma(k[q].y, x.x, ai);
-                    }
-                    y[fl] = cmk<C>(ar, ai);
+            for (int q = p; q < NP; ++q) {
+                const C k = __ldg(Kr + herm_index(NP, p, q) * 8);
+                yr[p] = fma(k.x, x[q].x, yr[p]);           // y_p += K_pq x_q
+                yr[p] = fma(-k.y, x[q].y, yr[p]);
+                yi[p] = fma(k.x, x[q].y, yi[p]);
+                yi[p] = fma(k.y, x[q].x, yi[p]);
+                if (q != p) {                              // y_q += conj(K_pq) x_p
+                    yr[q] = fma(k.x, x[p].x, yr[q]);
+                    yr[q] = fma(k.y, x[p].y, yr[q]);
+                    yi[q] = fma(k.x, x[p].y, yi[q]);
+                    yi[q] = fma(-k.y, x[p].x, yi[q]);
                 }
             }
         }
-        __syncthreads();
-        if (on) {
-            C* out = D + pp * P + ky;
 #pragma unroll
-            for (int fl = 0; fl < kMaxFramesPerBlock; ++fl)
-                if ((am >> fl) & 1u) out[fl * NPmax * P] = y[fl];
-        }
-        __syncthreads();
+        for (int p = 0; p < NP; ++p) col[p * P] = cmk<C>(yr[p], yi[p]);
     }
+    __syncthreads();                               // the inverse transforms read other threads' columns
 }
 
 template <typename C>
@@ -413,7 +401,6 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* scr = tw + P;
     C* D = scr + (Fused<PC>::ok ? 0 : kWarps * P); // [Bc][NPmax][P]
-    C* Ks = D + (size_t)Bc * NPmax * P;            // packed K of one round (Hermitian path)
     __shared__ int act[kMaxFramesPerBlock];
     const int kx = blockIdx.x;
     const int f0 = blockIdx.y * Bc;
@@ -479,9 +466,9 @@ k_cols_mul(MvmGeom g, int B, int Bc, const FrameState* st, const cplx_t<T>* __re
     __syncthreads();
     // block multiply: one thread per (ky, p), frames looped
     const C* Kc = K + (size_t)kx * NPin * P * NPout;
-    const C* Kh = K + (size_t)kx * P * (NPin * (NPin + 1) / 2);
+    const C* Kh = K + herm_offset(NPin, P, kx, 0, 0);
     if (herm) {
-#define TOMO_BMH(NP_) block_mul_herm<C, NP_, PC, NP_>(D, NPmax, P, am, Kh, Ks)
+#define TOMO_BMH(NP_) block_mul_herm<C, NP_, PC, NP_>(D, NPmax, P, nf, am, Kh)
         switch (NPin) {
             case 2: TOMO_BMH(2); break;
             case 4: TOMO_BMH(4); break;
@@ -524,8 +511,7 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
     if (g.NPin > 16) return cudaErrorInvalidValue;
     const int NPmax = g.NPin > g.NPout ? g.NPin : g.NPout;
     if (herm && (g.NPin != g.NPout || (g.NPin & 1) || g.NPin < 2 || g.NPin > 16)) return cudaErrorInvalidValue;
-    const size_t ks = herm ? sizeof(C) * (size_t)(kThreads / g.NPin) * (g.NPin * (g.NPin + 1) / 2) : 0;
-    const size_t fixed = sizeof(C) * (size_t)g.plan.P * (1 + (has_fused_plan(g.plan.P) ? 0 : kWarps)) + ks;
+    const size_t fixed = sizeof(C) * (size_t)g.plan.P * (1 + (has_fused_plan(g.plan.P) ? 0 : kWarps));
     const size_t per_frame = sizeof(C) * (size_t)NPmax * g.plan.P;
 #ifndef TOMO_COLS_BUDGET_KB
 #define TOMO_COLS_BUDGET_KB 72
@@ -1524,14 +1510,19 @@ cudaError_t precond_spectra(const Launch& L, int P, int NP, const double2* K64, 
 }
 
 // Packs a full NP x NP spectrum [nh][NP(q)][P][NP(p)] into the Hermitian
-// upper-triangle layout [nh][P][e(p <= q)], storing (K_pq + conj K_qp) / 2.
+// upper-triangle layout of block_mul_herm (herm_offset), storing
+// (K_pq + conj K_qp) / 2; the padding frequencies ky >= P are zero.
 __global__ void k_pack_hermitian(int P, int NP, const float2* __restrict__ Kf, float2* __restrict__ Kp) {
-    const int nh = P / 2 + 1, NE = NP * (NP + 1) / 2;
+    const int nh = P / 2 + 1, NE = NP * (NP + 1) / 2, P8 = (P + 7) / 8;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)nh * P * NE) return;
-    const int e = (int)(i % NE);
-    const size_t fk = i / NE;
-    const int ky = (int)(fk % P), kx = (int)(fk / P);
+    if (i >= herm_packed_elems(P, NP)) return;
+    const int ky = (int)(i % 8) + 8 * (int)((i / ((size_t)8 * NE)) % P8);
+    const int e = (int)((i / 8) % NE);
+    const int kx = (int)(i / ((size_t)8 * NE * P8));
+    if (ky >= P || kx >= nh) {
+        Kp[i] = make_float2(0.f, 0.f);
+        return;
+    }
     int p = 0;
     while (herm_index(NP, p + 1, p + 1) <= e && p + 1 < NP) ++p;
     const int q = p + (e - herm_index(NP, p, p));
@@ -1541,7 +1532,7 @@ __global__ void k_pack_hermitian(int P, int NP, const float2* __restrict__ Kf, f
 }
 
 cudaError_t pack_hermitian(const Launch& L, int P, int NP, const float2* Kfull, float2* Kpacked) {
-    const size_t total = (size_t)(P / 2 + 1) * P * (NP * (NP + 1) / 2);
+    const size_t total = herm_packed_elems(P, NP);
     k_pack_hermitian<<<(unsigned)((total + 255) / 256), 256, 0, L.stream>>>(P, NP, Kfull, Kpacked);
     count(L);
     return cudaGetLastError();

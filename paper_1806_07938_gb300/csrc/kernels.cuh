@@ -114,6 +114,11 @@ template <typename T>
 cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState* st,
                      const cplx_t<T>* X1T, cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw, bool herm);
 // Full [nh][NP][P][NP] spectrum -> Hermitian upper-triangle layout [nh][P][e].
+// Elements of the Hermitian-packed spectra of an NP x NP block operator on a
+// P x P torus: (P/2 + 1) kx x P padded to a multiple of 8 (ky) x NP (NP + 1) / 2.
+__host__ __device__ inline size_t herm_packed_elems(int P, int NP) {
+    return (size_t)(P / 2 + 1) * ((P + 7) / 8 * 8) * (NP * (NP + 1) / 2);
+}
 cudaError_t pack_hermitian(const Launch& L, int P, int NP, const float2* Kfull, float2* Kpacked);
 
 // Row-inverse pass to masked output (Sigma_ss): y = c_f crop/mask(IFFT rows) +
