@@ -1529,7 +1529,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
             CK(cudaMallocHost(&h->h_small, sizeof(double) * 9 * 64 * 64));
         }
         // small FP64 matrices, device and pinned host at the same offsets:
-        // [G] [norms] [H] [E] [T_G] [T_W] [Gw] [alpha / beta] [work]
+        // [G] [norms] [H] [E] [T_G] [T_W] [Gw] [alpha / beta]
         constexpr size_t kS = 4096;
         constexpr int kNormSlices = 16;
         double* dG = h->d_small;
@@ -1540,7 +1540,6 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
         double* dTW = dG + 5 * kS;
         double* dGw = dG + 6 * kS;
         double* dAB = dG + 7 * kS;                       // alpha, then beta
-        double* dWk = dG + 8 * kS;                       // T_G^T H (a product never writes its inputs)
         double* hs = h->h_small;
         const size_t BB = (size_t)B * B;
         std::vector<double> G(BB), Gw(BB), C, LG, LW, tol2(B);
@@ -1624,8 +1623,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
                 }
                 TRY(factor(dG, G, 1e-13, LG, dropG, dTG));
                 // alpha = G^+ P^T r = T_G T_G^T H on the device; x += P alpha, r -= A P alpha
-                CK(small_gemm(L, B, dTG, dH, dWk, true, 1.0));
-                CK(small_gemm(L, B, dTG, dWk, dAB, false, 1.0));
+                CK(gram_apply(L, B, dTG, dH, dAB, 1.0));
                 CK(block_combine(L, B, h->N, dAB, h->p, h->x, h->x));
                 CK(block_combine(L, B, h->N, dAB, h->Ap, h->r, h->r, -1.0));
                 ++block_iters;
@@ -1635,8 +1633,7 @@ tomo_status solve_chunk(tomo_handle* h, const float* s, int B, const tomo_solve_
                 if (pcg) { TRY(apply_M(h->r, h->z)); Z = h->z; }
                 // beta = -G^+ (A P)^T z; next W = z + P beta
                 CK(gram(L, B, h->N, h->Ap, Z, dE, h->d_gram_part));
-                CK(small_gemm(L, B, dTG, dE, dWk, true, 1.0));
-                CK(small_gemm(L, B, dTG, dWk, dAB, false, -1.0));
+                CK(gram_apply(L, B, dTG, dE, dAB, -1.0));
                 CK(block_combine(L, B, h->N, dAB, h->p, Z, h->w));
                 W = h->w;
                 CK(gram(L, B, h->N, W, W, dGw, h->d_gram_part));

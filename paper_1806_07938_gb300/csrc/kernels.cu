@@ -295,9 +295,11 @@ __device__ __forceinline__ void block_mul(C* D, int NPmax, int P, int nf, const 
 
 // Hermitian variant for Sigma_ss (NP x NP blocks with K_qp = conj K_pq): only
 // the upper triangle is stored, entry e(p, q) = herm_index(NP, p, q) for
-// p <= q, with the frequencies ky interleaved in groups of eight:
-// [kx][ky / 8][e][ky % 8] (herm_offset; ky padded to a multiple of 8), so that
-// the eight ky of a warp read one contiguous 64-byte segment per entry.
+// p <= q, in pairs of consecutive entries with the frequencies ky interleaved
+// in groups of eight: [kx][ky / 8][e / 2][ky % 8][e % 2] (herm_offset; ky
+// padded to a multiple of 8, e to an even count), so that one 16-byte load
+// gives a thread two entries and the eight ky of a warp read one contiguous
+// 128-byte segment.
 //
 // One thread per (ky, frame): it reads its x_q(ky) once, streams the packed
 // entries of K(kx, ky) from global memory (L2; the frames of a ky share them
@@ -307,10 +309,22 @@ __device__ __forceinline__ void block_mul(C* D, int NPmax, int P, int nf, const 
 // Each y_p is accumulated over q in ascending order.
 __host__ __device__ constexpr int herm_index(int NP, int p, int q) { return p * NP - p * (p - 1) / 2 + (q - p); }
 
+__host__ __device__ constexpr int herm_pairs(int NP) { return (NP * (NP + 1) / 2 + 1) / 2; }
+
 __host__ __device__ inline size_t herm_offset(int NP, int P, int kx, int ky, int e) {
-    const int NE = NP * (NP + 1) / 2;
     const int P8 = (P + 7) / 8;
-    return (((size_t)kx * P8 + (ky >> 3)) * NE + e) * 8 + (ky & 7);
+    return ((((size_t)kx * P8 + (ky >> 3)) * herm_pairs(NP) + (e >> 1)) * 8 + (ky & 7)) * 2 + (e & 1);
+}
+
+// Two consecutive complex values (16-byte aligned) in one load where they fit.
+__device__ __forceinline__ void load_pair(const float2* src, float2 (&v)[2]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(src));
+    v[0] = make_float2(t.x, t.y);
+    v[1] = make_float2(t.z, t.w);
+}
+__device__ __forceinline__ void load_pair(const double2* src, double2 (&v)[2]) {
+    v[0] = __ldg(src);
+    v[1] = __ldg(src + 1);
 }
 
 template <typename C, int NP, int PS, int NPM>
@@ -333,11 +347,14 @@ __device__ __forceinline__ void block_mul_herm(C* D, int NPmax_rt, int P_rt, int
             yr[q] = 0;
             yi[q] = 0;
         }
+        C kpair[2];
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
 #pragma unroll
             for (int q = p; q < NP; ++q) {
-                const C k = __ldg(Kr + herm_index(NP, p, q) * 8);
+                const int e = herm_index(NP, p, q);
+                if ((e & 1) == 0) load_pair(Kr + (e >> 1) * 16, kpair);
+                const C k = kpair[e & 1];
                 yr[p] = fma(k.x, x[q].x, yr[p]);           // y_p += K_pq x_q
                 yr[p] = fma(-k.y, x[q].y, yr[p]);
                 yi[p] = fma(k.x, x[q].y, yi[p]);
@@ -1513,13 +1530,14 @@ cudaError_t precond_spectra(const Launch& L, int P, int NP, const double2* K64, 
 // upper-triangle layout of block_mul_herm (herm_offset), storing
 // (K_pq + conj K_qp) / 2; the padding frequencies ky >= P are zero.
 __global__ void k_pack_hermitian(int P, int NP, const float2* __restrict__ Kf, float2* __restrict__ Kp) {
-    const int nh = P / 2 + 1, NE = NP * (NP + 1) / 2, P8 = (P + 7) / 8;
+    const int nh = P / 2 + 1, NE = NP * (NP + 1) / 2, P8 = (P + 7) / 8, NE2 = herm_pairs(NP);
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= herm_packed_elems(P, NP)) return;
-    const int ky = (int)(i % 8) + 8 * (int)((i / ((size_t)8 * NE)) % P8);
-    const int e = (int)((i / 8) % NE);
-    const int kx = (int)(i / ((size_t)8 * NE * P8));
-    if (ky >= P || kx >= nh) {
+    // i = (((kx P8 + ky / 8) NE2 + e / 2) 8 + ky % 8) 2 + e % 2
+    const int e = 2 * (int)((i / 16) % NE2) + (int)(i % 2);
+    const int ky = (int)((i / 2) % 8) + 8 * (int)((i / ((size_t)16 * NE2)) % P8);
+    const int kx = (int)(i / ((size_t)16 * NE2 * P8));
+    if (ky >= P || kx >= nh || e >= NE) {
         Kp[i] = make_float2(0.f, 0.f);
         return;
     }

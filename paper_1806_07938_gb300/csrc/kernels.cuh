@@ -115,9 +115,10 @@ cudaError_t cols_mul(const Launch& L, const MvmGeom& g, int B, const FrameState*
                      const cplx_t<T>* X1T, cplx_t<T>* Y1T, const cplx_t<T>* K, const cplx_t<T>* tw, bool herm);
 // Full [nh][NP][P][NP] spectrum -> Hermitian upper-triangle layout [nh][P][e].
 // Elements of the Hermitian-packed spectra of an NP x NP block operator on a
-// P x P torus: (P/2 + 1) kx x P padded to a multiple of 8 (ky) x NP (NP + 1) / 2.
+// P x P torus: (P/2 + 1) kx x P padded to a multiple of 8 (ky) x NP (NP + 1) / 2
+// padded to an even count.
 __host__ __device__ inline size_t herm_packed_elems(int P, int NP) {
-    return (size_t)(P / 2 + 1) * ((P + 7) / 8 * 8) * (NP * (NP + 1) / 2);
+    return (size_t)(P / 2 + 1) * ((P + 7) / 8 * 8) * ((NP * (NP + 1) / 2 + 1) / 2 * 2);
 }
 cudaError_t pack_hermitian(const Launch& L, int P, int NP, const float2* Kfull, float2* Kpacked);
 
@@ -293,7 +294,8 @@ cudaError_t gram(const Launch& L, int B, int N, const float* U, const float* V, 
 cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const float* U, const float* Y0, float* Y,
                           double scale = 1.0);
 // Y = scale op(A) X for B x B FP64 matrices, op(A) = A or A^T (Y must not alias A or X).
-cudaError_t small_gemm(const Launch& L, int B, const double* A, const double* X, double* Y, bool transA, double scale);
+// Y = scale T (T^T X), B x B row-major FP64 (T^T X is never stored)
+cudaError_t gram_apply(const Launch& L, int B, const double* T, const double* X, double* Y, double scale);
 cudaError_t row_norms(const Launch& L, int B, int N, const float* X, double* out, int slices);
 // Y_j = f[j] X_j (device FP64 factors; Y may alias X).
 cudaError_t scale_rows(const Launch& L, int B, int N, const double* f, const float* X, float* Y);

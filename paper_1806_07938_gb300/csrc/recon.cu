@@ -277,15 +277,23 @@ k_gram_part(int B, int N, const float* __restrict__ U, const float* __restrict__
 
 // G[i][j] = sum over the partial tiles: a block of 256 threads serves 32
 // entries; warp t sums tiles t, t + 8, t + 16, ... of its lane's entry
-// (coalesced across the warp), and the eight sums are added in a fixed order.
+// (coalesced across the warp), and all sums are added in a fixed order.
 __global__ void __launch_bounds__(256)
 k_gram_reduce(int B, int splits, const double* __restrict__ part, double* __restrict__ G) {
     __shared__ double red[8][32];
     const int t = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int e = blockIdx.x * 32 + lane;
-    double s = 0.0;
-    for (int z = t; z < splits; z += 8) s += part[(size_t)z * kBlockMax * kBlockMax + e];
-    red[t][lane] = s;
+    // four independent running sums (tiles t, t + 8, t + 16, t + 24 of each
+    // group of 32), so that four loads are in flight per thread
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    int z = t;
+    for (; z + 24 < splits; z += 32)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s4[u] += part[(size_t)(z + 8 * u) * kBlockMax * kBlockMax + e];
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+        if (z + 8 * u < splits) s4[u] += part[(size_t)(z + 8 * u) * kBlockMax * kBlockMax + e];
+    red[t][lane] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     __syncthreads();
     if (t == 0) {
         const double v = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
@@ -331,15 +339,26 @@ k_block_combine(int B, int N, const double* __restrict__ C, double scale, const 
     }
 }
 
-// Y = scale * op(A) X for B x B FP64 matrices (row-major), op(A) = A or A^T:
-// one block per row of Y, one thread per column.
-__global__ void k_small_gemm(int B, const double* __restrict__ A, const double* __restrict__ X, double* __restrict__ Y,
-                             int transA, double scale) {
-    const int i = blockIdx.x, j = threadIdx.x;
-    if (i >= B || j >= B) return;
-    double acc = 0.0;
-    for (int k = 0; k < B; ++k) acc += (transA ? A[k * B + i] : A[i * B + k]) * X[k * B + j];
-    Y[i * B + j] = scale * acc;
+// Y = scale * T (T^T X) for B x B FP64 matrices (row-major): one block per
+// column j of Y, one thread per row.  The inner product T^T X[:, j] is kept
+// in shared memory; both sums run over k in ascending order.
+__global__ void k_gram_apply(int B, const double* __restrict__ T, const double* __restrict__ X,
+                             double* __restrict__ Y, double scale) {
+    __shared__ double w[kBlockMax];
+    const int j = blockIdx.x, i = threadIdx.x;
+    if (i < B) {
+        double acc = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < B; ++k) acc += T[k * B + i] * X[k * B + j];
+        w[i] = acc;
+    }
+    __syncthreads();
+    if (i < B) {
+        double acc = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < B; ++k) acc += T[i * B + k] * w[k];
+        Y[i * B + j] = scale * acc;
+    }
 }
 
 // Y[j][k] = f[j] X[j][k] (per-row scale; Y may alias X)
@@ -350,16 +369,19 @@ __global__ void k_scale_rows(int B, int N, const double* __restrict__ f, const f
         Y[(size_t)j * N + k] = a * X[(size_t)j * N + k];
 }
 
-// out[j][s] = sum over the s-th of S column slices of X[j][k]^2 (FP64)
+// out[j][s] = sum over the s-th of S column slices of X[j][k]^2
 __global__ void k_row_norms(int N, int S, const float* __restrict__ X, double* __restrict__ out) {
     __shared__ double red[8];
     const int b = blockIdx.x, sl = blockIdx.y;
     const int k0 = (int)((long long)N * sl / S), k1 = (int)((long long)N * (sl + 1) / S);
-    double acc = 0.0;
+    // FP32 per-thread partials (a few tens of squares), FP64 from the warp sums
+    // on (GB300's FP64 rate is ~1/64 of its FP32 rate)
+    float a32 = 0.f;
     for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-        const double v = X[(size_t)b * N + k];
-        acc += v * v;
+        const float v = X[(size_t)b * N + k];
+        a32 = fmaf(v, v, a32);
     }
+    double acc = a32;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -591,9 +613,9 @@ cudaError_t block_combine(const Launch& L, int B, int N, const double* C, const 
     return cudaGetLastError();
 }
 
-cudaError_t small_gemm(const Launch& L, int B, const double* A, const double* X, double* Y, bool transA, double scale) {
+cudaError_t gram_apply(const Launch& L, int B, const double* T, const double* X, double* Y, double scale) {
     if (B < 1 || B > kBlockMax) return cudaErrorInvalidValue;
-    k_small_gemm<<<B, kBlockMax, 0, L.stream>>>(B, A, X, Y, transA ? 1 : 0, scale);
+    k_gram_apply<<<B, kBlockMax, 0, L.stream>>>(B, T, X, Y, scale);
     count2(L);
     return cudaGetLastError();
 }
