@@ -12,7 +12,7 @@
 //     during the FFTs instead of before them.  Row-inverse: the plane's half
 //     spectra [kx][row] (45 KB at P = 150).  Row-forward in CG mode: the
 //     plane's slices of p, r, A p and x (4 x 15.9 KB).
-//   * the vector gather of the row-inverse pass reads four entries per load.
+//   * the vector scatter and gather read four entries per load.
 // Every wait on a copy is bounded (kMaxWaitPolls); on expiry the block sets
 // g_wait_error, waits (again bounded) for its copy and returns.
 #include <cstdio>
@@ -62,6 +62,37 @@ __device__ __forceinline__ double bsum32(float v, double* red) {
     return out;
 }
 
+// bsum32 for three values at once (one pair of block barriers); red holds
+// 3 x (warps) doubles.  Thread 0 returns the sums in out.
+__device__ __forceinline__ void bsum32x3(float v0, float v1, float v2, double* red, double (&out)[3]) {
+    float s[3] = {v0, v1, v2}, c[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float t = __shfl_down_sync(0xffffffffu, s[q], o);
+            const float tc = __shfl_down_sync(0xffffffffu, c[q], o);
+            const float u = s[q] + t;
+            const float bp = u - s[q];
+            const float err = (s[q] - (u - bp)) + (t - bp);
+            s[q] = u;
+            c[q] += tc + err;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) red[q * nw + warp] = (double)s[q] + (double)c[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q) out[q] = 0.0;
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            for (int w = 0; w < nw; ++w) out[q] += red[q * nw + w];
+}
+
 // Thread 0 waits for the barrier phase (bounded), the block learns the
 // outcome through shared memory; then every thread observes the completed
 // phase itself (immediate), which makes the copied bytes visible to it.
@@ -96,7 +127,7 @@ k_rows_inv_pp(MvmGeom g, MaskTables mt, int items, const FrameState* __restrict_
     using C = float2;
     constexpr int P = PC, RS = P | 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ double red[kWarps];
+    __shared__ double red[3 * kWarps];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int ok;
     const int m = g.m, nh = g.nh, NPo = g.NPout;
@@ -187,13 +218,14 @@ k_rows_inv_pp(MvmGeom g, MaskTables mt, int items, const FrameState* __restrict_
             }
         }
         if (cgm) {
-            double* dp = cg.dot_part + (size_t)t * 3;
-            const double s0 = bsum32(acc, red);
-            if (threadIdx.x == 0) dp[0] = s0;
-            const double s1 = bsum32(acc_r, red);
-            if (threadIdx.x == 0) dp[1] = s1;
-            const double s2 = bsum32(acc_a, red);
-            if (threadIdx.x == 0) dp[2] = s2;
+            double sums[3];
+            bsum32x3(acc, acc_r, acc_a, red, sums);
+            if (threadIdx.x == 0) {
+                double* dp = cg.dot_part + (size_t)t * 3;
+                dp[0] = sums[0];
+                dp[1] = sums[1];
+                dp[2] = sums[2];
+            }
         }
         __syncthreads();                       // F is rebuilt for the next plane
         t = tn;
@@ -243,39 +275,85 @@ k_rows_fwd_pp(MvmGeom g, MaskTables mt, int items, const float* __restrict__ x, 
     if (t >= items) return;
     if (threadIdx.x == 0) fetch(t);
     uint32_t parity = 0;
+    const int n4 = nvs >> 2;
+    const int4* __restrict__ rc4 = reinterpret_cast<const int4*>(mt.rowcol);
+    auto put = [&](int rc, float v) {
+        const int row = rc >> 16, col = rc & 0xffff;
+        reinterpret_cast<float*>(F + (row >> 1) * RS + col)[row & 1] = v;
+    };
     while (t < items) {
         const int f = t / NPi;
-        for (int i = threadIdx.x; i < npl * RS; i += blockDim.x) F[i] = make_float2(0.f, 0.f);
+        // only the first n columns are read by the pruned row transforms
+        for (int j = warp; j < npl; j += kWarps)
+            for (int c = lane; c < n; c += 32) F[j * RS + c] = make_float2(0.f, 0.f);
         if (!block_wait(&bar, parity, &ok)) return;    // (includes the barrier that orders the zeroing)
         parity ^= 1u;
         const size_t vb = (size_t)t * nvs;
         float rr = 0.f;                                   // per thread FP32 (~16 products), FP64 across
+        // four consecutive entries per thread and step, the mask entries of
+        // two steps loaded ahead (the vector stores below may alias nothing
+        // the loads read, but the compiler cannot know that)
+        constexpr int U = 2;
         if (MODE == 1) {
             const float alpha = (float)st[f].alpha, beta = (float)st[f].beta;
-            const float* Vp = V;
-            const float* Vr = V + nvs;
-            const float* VAp = V + 2 * nvs;
-            const float* Vx = V + 3 * nvs;
-            for (int e = threadIdx.x; e < nvs; e += blockDim.x) {
-                const float pe = Vp[e];
-                float re = Vr[e];
-                if (alpha != 0.f) {
-                    cg.x[vb + e] = Vx[e] + alpha * pe;
-                    re -= alpha * VAp[e];
-                    cg.r[vb + e] = re;
+            const float4* Vp = reinterpret_cast<const float4*>(V);
+            const float4* Vr = Vp + n4;
+            const float4* VAp = Vp + 2 * n4;
+            const float4* Vx = Vp + 3 * n4;
+            float4* x4 = reinterpret_cast<float4*>(cg.x + vb);
+            float4* r4 = reinterpret_cast<float4*>(cg.r + vb);
+            float4* p4 = reinterpret_cast<float4*>(cg.p + vb);
+            for (int i0 = threadIdx.x; i0 < n4; i0 += U * blockDim.x) {
+                int4 rc[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (i0 + u * (int)blockDim.x < n4) rc[u] = __ldg(rc4 + i0 + u * blockDim.x);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i >= n4) continue;
+                    const float4 pe = Vp[i];
+                    float4 re = Vr[i];
+                    if (alpha != 0.f) {
+                        const float4 ap = VAp[i], xv = Vx[i];
+                        x4[i] = make_float4(xv.x + alpha * pe.x, xv.y + alpha * pe.y, xv.z + alpha * pe.z,
+                                            xv.w + alpha * pe.w);
+                        re.x -= alpha * ap.x;
+                        re.y -= alpha * ap.y;
+                        re.z -= alpha * ap.z;
+                        re.w -= alpha * ap.w;
+                        r4[i] = re;
+                    }
+                    const float4 pn = make_float4(re.x + beta * pe.x, re.y + beta * pe.y, re.z + beta * pe.z,
+                                                  re.w + beta * pe.w);
+                    p4[i] = pn;
+                    rr = fmaf(re.x, re.x, rr);
+                    rr = fmaf(re.y, re.y, rr);
+                    rr = fmaf(re.z, re.z, rr);
+                    rr = fmaf(re.w, re.w, rr);
+                    put(rc[u].x, pn.x);
+                    put(rc[u].y, pn.y);
+                    put(rc[u].z, pn.z);
+                    put(rc[u].w, pn.w);
                 }
-                const float pn = re + beta * pe;
-                cg.p[vb + e] = pn;
-                rr = fmaf(re, re, rr);
-                const int rc = mt.rowcol[e];
-                const int row = rc >> 16, col = rc & 0xffff;
-                reinterpret_cast<float*>(F + (row >> 1) * RS + col)[row & 1] = pn;
             }
         } else {
-            for (int e = threadIdx.x; e < nvs; e += blockDim.x) {
-                const int rc = mt.rowcol[e];
-                const int row = rc >> 16, col = rc & 0xffff;
-                reinterpret_cast<float*>(F + (row >> 1) * RS + col)[row & 1] = V[e];
+            const float4* V4 = reinterpret_cast<const float4*>(V);
+            for (int i0 = threadIdx.x; i0 < n4; i0 += U * blockDim.x) {
+                int4 rc[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (i0 + u * (int)blockDim.x < n4) rc[u] = __ldg(rc4 + i0 + u * blockDim.x);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i >= n4) continue;
+                    const float4 v = V4[i];
+                    put(rc[u].x, v.x);
+                    put(rc[u].y, v.y);
+                    put(rc[u].z, v.z);
+                    put(rc[u].w, v.w);
+                }
             }
         }
         __syncthreads();
@@ -389,7 +467,9 @@ cudaError_t rows_fwd_pp(const Launch& L, const MvmGeom& g, const MaskTables& mt,
                         bool* used) {
     *used = false;
     const int P = g.plan.P;
-    if (!(pp_mask() & 2) || B < 1 || !has_fused_plan(P) || (mt.n_vs & 3) != 0 || !aligned16(X1T)) return cudaSuccess;
+    if (!(pp_mask() & 2) || B < 1 || !has_fused_plan(P) || (mt.n_vs & 3) != 0 || !aligned16(X1T) ||
+        !aligned16(mt.rowcol))
+        return cudaSuccess;
     const int mode = cg && cg->p ? cg->mode : 0;
     if (mode != 0 && mode != 1) return cudaSuccess;
     if (mode == 1 && !(aligned16(cg->p) && aligned16(cg->r) && aligned16(cg->Ap) && aligned16(cg->x)))
