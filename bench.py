@@ -957,6 +957,19 @@ def run_ours(args):
                                if roof["bound"] == "alu" else f"HBM copy, {pk['src']}")
         roof["avg_launch_us"] = 1000.0 * kms[dom] / max(1, kn[dom])
         roof["kernel_ms"] = {k: round(v, 3) for k, v in kms.items()}
+        # every pass of the product against both bounds (algorithmic bytes and
+        # flops of kernel_model over the same CUDA-event time); "bound" is the
+        # one the pass's arithmetic intensity puts it under
+        per = {}
+        for k in ("rows_fwd", "cols_mul", "rows_inv"):
+            mk, sk = model[k], kms[k] / 1000.0
+            fk = mk["flops"] * frame_iters
+            bk = mk["bytes"] * frame_iters + mk["per_launch_bytes"] * kn[k]
+            per[k] = {"avg_launch_us": round(1e6 * sk / max(1, kn[k]), 2),
+                      "hbm_gbs": round(bk / sk / 1e9, 1), "hbm_frac": round(bk / sk / 1e9 / pk["hbm_gbs"], 4),
+                      "alu_tflops": round(fk / sk / 1e12, 2), "alu_frac": round(fk / sk / 1e12 / alu_peak, 4),
+                      "bound": "alu" if fk / bk > balance else "hbm"}
+        roof["per_kernel"] = per
         roof["whole_product"] = whole_product(model, F, total_ms / args.steps, float(iters.mean()), pk["hbm_gbs"],
                                               alu_peak)
 
