@@ -71,6 +71,12 @@ __device__ __forceinline__ void bulk_load_more(void* dst, const void* src, uint3
                  : "memory");
 }
 
+// Starts fetching `bytes` of global memory into L2 (no shared memory, no
+// completion to wait for; 16-byte aligned address, size a multiple of 16).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Waits for the barrier phase with the given parity; false after kMaxWaitPolls polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint32_t a = smem_addr(bar);

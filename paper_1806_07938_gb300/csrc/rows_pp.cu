@@ -10,8 +10,10 @@
 //     asynchronous copy (cp.async.bulk, completion counted on an mbarrier)
 //     while the block transforms the current one, so the loads are in flight
 //     during the FFTs instead of before them.  Row-inverse: the plane's half
-//     spectra [kx][row] (45 KB at P = 150).  Row-forward in CG mode: the
-//     plane's slices of p, r, A p and x (4 x 15.9 KB).
+//     spectra [kx][row] (45 KB at P = 150), and its slices of the input and
+//     of r fetched into L2 (cp.async.bulk.prefetch.L2) for the gather.
+//     Row-forward in CG mode: the plane's slices of p, r, A p and x
+//     (4 x 15.9 KB).
 //   * the vector scatter and gather read four entries per load.
 // Every wait on a copy is bounded (kMaxWaitPolls); on expiry the block sets
 // g_wait_error, waits (again bounded) for its copy and returns.
@@ -143,10 +145,22 @@ k_rows_inv_pp(MvmGeom g, MaskTables mt, int items, const FrameState* __restrict_
     for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = twg[i];
     __syncthreads();
     if (t >= items) return;
-    if (threadIdx.x == 0) bulk_load(S, Y1T + (size_t)t * slab, (uint32_t)(slab * sizeof(C)), &bar);
     const bool cgm = cg.p != nullptr;
     // second partner of the partial sums: r (CG, PCG) or the direction's A p (MINRES)
     const float* __restrict__ vr = cg.mode == 3 ? cg.Ap : cg.r;
+    // the vector slices the gather of item it reads, fetched into L2 with its
+    // half spectra (they are read from DRAM otherwise: the column pass between
+    // the two row passes evicts them)
+    const uint32_t vbytes = (uint32_t)(mt.n_vs * sizeof(float));
+    auto prefetch_vectors = [&](int it) {
+        const size_t o = (size_t)it * mt.n_vs;
+        if (xin) bulk_prefetch_l2(xin + o, vbytes);
+        if (cgm) bulk_prefetch_l2(vr + o, vbytes);
+    };
+    if (threadIdx.x == 0) {
+        bulk_load(S, Y1T + (size_t)t * slab, (uint32_t)(slab * sizeof(C)), &bar);
+        prefetch_vectors(t);
+    }
     const int n4 = mt.n_vs >> 2;
     uint32_t parity = 0;
     while (t < items) {
@@ -166,6 +180,7 @@ k_rows_inv_pp(MvmGeom g, MaskTables mt, int items, const FrameState* __restrict_
         if (threadIdx.x == 0 && tn < items) {
             fence_async_shared();
             bulk_load(S, Y1T + (size_t)tn * slab, (uint32_t)(slab * sizeof(C)), &bar);
+            prefetch_vectors(tn);
         }
         for (int g0 = warp * kPPRound; g0 < npair; g0 += kWarps * kPPRound)
             fft_rounds<PC, C, false, kPPRound>(F + g0 * RS, RS, min(kPPRound, npair - g0), g.plan, tw, nullptr, lane,
