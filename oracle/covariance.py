@@ -23,6 +23,13 @@ check for.
 Vector layout (Sec. 2.D, Eq. for Sigma_{s_i s_j}): guide stars in order, each
 as [x-slopes over valid subapertures ; y-slopes over valid subapertures],
 subapertures in row-major order.
+
+Guide stars may sample the pupil on grids of their own (the uneven MOAO
+system of natural stars on 10 x 10 grids beside laser stars on 74 x 74,
+Sec. 2.D: blocks between stars of different grids or altitudes are not
+Toeplitz): cfg["gs_n"] lists the subapertures across the pupil of each guide
+star (default cfg["n"] for all).  The point-covariance sum above is the same
+for any mix; only the slope points change.
 """
 
 import math
@@ -35,6 +42,16 @@ from . import turbulence as turb
 
 def _gs(cfg):
     return [(float(ax), float(ay), float(h)) for (ax, ay, h) in cfg["gs"]]
+
+
+def gs_grid(cfg, g):
+    """Subapertures across the pupil of guide star g (cfg["gs_n"], else cfg["n"])."""
+    return int(cfg.get("gs_n", [cfg["n"]] * len(cfg["gs"]))[g])
+
+
+def uniform_grid(cfg):
+    """True if every guide star samples the pupil on the cfg["n"] grid."""
+    return all(gs_grid(cfg, g) == cfg["n"] for g in range(len(cfg["gs"])))
 
 
 def cone_factor(H, h):
@@ -56,11 +73,12 @@ def slope_points(cfg):
     (K = 2 Hudgin, 4 Fried), w (N, K) the weights, gsidx (N,) the guide-star
     index of each slope.
     """
-    n, D, eps = cfg["n"], cfg["D"], cfg["obstruction"]
-    d = D / n
-    c = geo.subaperture_centres(n, D, eps)
+    D, eps = cfg["D"], cfg["obstruction"]
     pts, w, gi = [], [], []
     for g in range(len(cfg["gs"])):
+        n = gs_grid(cfg, g)
+        d = D / n
+        c = geo.subaperture_centres(n, D, eps)
         for comp in (0, 1):
             off, wt = slope_stencil(cfg, comp, d)
             for cc in c:
@@ -145,6 +163,8 @@ def add_noise(A, cfg, scale=1.0):
     if C is None:
         A[np.diag_indices_from(A)] += scale * noise_variance(cfg)
         return A
+    if not uniform_grid(cfg):
+        raise NotImplementedError("elongated-spot noise blocks need one grid for all guide stars")
     C = np.asarray(C, dtype=np.float64)
     valid = geo.valid_list(geo.subaperture_mask(cfg["n"], cfg["obstruction"]))
     nv = len(valid)

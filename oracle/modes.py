@@ -38,6 +38,8 @@ def _mode(name, xy):
 
 def slope_modes(cfg):
     """Z_s of one WFS: (2 n_vs, 3), the two-point slopes of tip, tilt, focus."""
+    if not cov.uniform_grid(cfg):
+        raise NotImplementedError("mode removal here takes one grid for all guide stars")
     pts, w, gsidx = cov.slope_points(cfg)
     one = gsidx == 0
     pts, w = pts[one], w[one]

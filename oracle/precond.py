@@ -21,6 +21,8 @@ from . import turbulence as turb
 
 def periodised_generators(cfg, P):
     """t[p, q, di, dj] for lags di, dj in [-P/2, P/2) (array index lag + P/2)."""
+    if not cov.uniform_grid(cfg):
+        raise NotImplementedError("the block-circulant preconditioner needs one grid for all guide stars")
     n, D = cfg["n"], cfg["D"]
     d = D / n
     gs = cfg["gs"]
