@@ -85,3 +85,74 @@ def test_uniform_grid_only_parts_refuse_mixed_grids():
         modes.slope_modes(cfg)
     with pytest.raises(NotImplementedError):
         cov.add_noise(np.zeros((2, 2)), dict(cfg, noise_cov=np.zeros((3, 9, 9, 3))))
+
+
+def _empirical_mixed(cfg, n_screens):
+    """Sample covariance of two-point slopes traced through simulated
+    single-layer screens, each star on its own grid (rays traced here, not by
+    the oracle: pupil point p of star (alpha, H) lands at (1 - h/H) p + h alpha)."""
+    from paper_1806_07938_gb300 import workloads as W
+    D = cfg["D"]
+    h, _ = cfg["layers"][0]
+    pts = []
+    for g, (ax, ay, H) in enumerate(cfg["gs"]):
+        n = cfg["gs_n"][g]
+        d = D / n
+        gam = 1.0 - h / H if H > 0 else 1.0
+        for comp in (0, 1):
+            off = np.zeros(2)
+            off[comp] = d / 2
+            for c in geo.subaperture_centres(n, D, cfg["obstruction"]):
+                shift = h * np.array([ax, ay])
+                pts.append([gam * (c + off) + shift, gam * (c - off) + shift])
+    pts = np.array(pts)
+    pix, N = D / 6 / 32, 512
+    rng = np.random.Generator(np.random.Philox(key=[13, 17]))
+    S = []
+    for _ in range(n_screens // 2):
+        for scr in W.screen_pair(rng, N, pix, cfg["r0"], cfg["L0"]):
+            sh = rng.uniform(0, N * pix, size=2)
+            a = W.bilinear(scr, pix, pts[:, 0, 0] + sh[0], pts[:, 0, 1] + sh[1])
+            b = W.bilinear(scr, pix, pts[:, 1, 0] + sh[0], pts[:, 1, 1] + sh[1])
+            S.append(a - b)
+    S = np.array(S)
+    return S.T @ S / len(S)
+
+
+def test_cross_block_matches_simulated_screens():
+    # a laser star on a 6 x 6 grid and a natural star on a 2 x 2 grid in
+    # nearby directions, one layer at 2 km (overlapping footprints, strongly
+    # correlated slopes): the oracle's whole matrix, and its cross block in
+    # particular, against the sample covariance of slopes on simulated
+    # screens; the cross block computed as if the natural star's slopes
+    # spanned the fine grid's subaperture size fits far worse
+    from paper_1806_07938_gb300 import workloads as W
+    cfg = dict(name="mc_mixed", D=1.5, obstruction=0.0, n=6, r0=0.15, L0=1.0, layers=[(2e3, 1.0)],
+               gs=[(5 * W.ARCSEC, 0.0, 90e3), (-5 * W.ARCSEC, 5 * W.ARCSEC, 0.0)], gs_n=[6, 2],
+               targets=[(0.0, 0.0)], noise_sigma=[0.0, 0.0])
+    C = cov.css_dense(cfg)
+    M = 4000
+    emp = _empirical_mixed(cfg, M)
+    nl = 2 * int(geo.subaperture_mask(6, 0.0).sum())
+
+    def z2(model, sl):
+        d = np.diag(C)
+        var = (np.outer(d, d) + C ** 2) / M
+        return float(np.mean(((emp - model) ** 2 / var)[sl]))
+    cross = (slice(0, nl), slice(nl, C.shape[0]))
+    # the wrong model: the natural star's slopes over fine-grid subaperture size
+    wrong = dict(cfg, gs_n=[6, 6])
+    Cw_full = cov.css_dense(wrong)
+    cen6 = geo.subaperture_centres(6, 1.5, 0.0)
+    cen2 = geo.subaperture_centres(2, 1.5, 0.0)
+    # the fine-grid natural-star slopes nearest the coarse centres stand in for them
+    pick = [int(np.argmin(np.hypot(*(cen6 - c).T))) for c in cen2]
+    nf = len(cen6)
+    rows = [nl + comp * nf + k for comp in (0, 1) for k in pick]
+    Cw = C.copy()
+    Cw[:nl, nl:] = Cw_full[:nl][:, rows]
+    good = z2(C, (slice(None), slice(None)))
+    good_x, bad_x = z2(C, cross), z2(Cw, cross)
+    print(good, good_x, bad_x)
+    assert good < 2.5 and good_x < 2.5
+    assert bad_x > 4 * good_x
