@@ -143,12 +143,17 @@ def _clean_frame(cfg, seed, f, screen_px, grids, shifts=None):
     return _sample(cfg, _screens(cfg, seed, f, screen_px), grids, shifts)
 
 
-def _sample(cfg, screens, grids, shifts=None):
-    n, D = cfg["n"], cfg["D"]
-    pix = D / n / 2.0
+def _sample(cfg, screens, grids, shifts=None, stars=None):
+    """Noiseless slopes [gs][x|y][n][n] on ``grids`` (stars: the guide-star
+    indices to sample, default all; the screens' pixel is D / cfg["n"] / 2)."""
+    D = cfg["D"]
+    pix = D / cfg["n"] / 2.0
     (cx, cy), (vx, vy), (hx, hy) = grids
-    out = np.zeros((len(cfg["gs"]), 2, n, n))
-    for g, (ax, ay, H) in enumerate(cfg["gs"]):
+    stars = range(len(cfg["gs"])) if stars is None else stars
+    n = vx.shape[0]
+    out = np.zeros((len(stars), 2, n, n))
+    for o, g in enumerate(stars):
+        ax, ay, H = cfg["gs"][g]
         pc = np.zeros_like(cx)
         pv = np.zeros_like(vx)
         ph = np.zeros_like(hx)
@@ -165,8 +170,8 @@ def _sample(cfg, screens, grids, shifts=None):
         left = (pc[:-1, :-1] + 2.0 * pv[:, :-1] + pc[1:, :-1]) / 4.0
         top = (pc[1:, :-1] + 2.0 * ph[1:, :] + pc[1:, 1:]) / 4.0
         bottom = (pc[:-1, :-1] + 2.0 * ph[:-1, :] + pc[:-1, 1:]) / 4.0
-        out[g, 0] = right - left
-        out[g, 1] = top - bottom
+        out[o, 0] = right - left
+        out[o, 1] = top - bottom
     return out
 
 
@@ -201,8 +206,8 @@ def slope_frames(cfg, n_frames, seed=0, screen_px=512, first=0):
     return noisy, sigma
 
 
-def _grids(cfg):
-    n, D = cfg["n"], cfg["D"]
+def _grids(cfg, n=None):
+    n, D = (cfg["n"] if n is None else n), cfg["D"]
     d = D / n
     e = (np.arange(n + 1) - n / 2.0) * d
     m = (np.arange(n) + 0.5 - n / 2.0) * d
@@ -210,6 +215,48 @@ def _grids(cfg):
     vy, vx = np.meshgrid(m, e, indexing="ij")
     hy, hx = np.meshgrid(e, m, indexing="ij")
     return ((cx, cy), (vx, vy), (hx, hy))
+
+
+def slope_frames_mixed(cfg, n_frames, seed=0, screen_px=512):
+    """Noisy valid slopes [frame][N] (float64) in the solver's vector layout
+    for guide stars on grids of their own (cfg["gs_n"]: subapertures across
+    the pupil per star, default cfg["n"]; cfg["n"] sets the screens' pixel,
+    so it should be the finest grid), and the per-star noise sigma.
+
+    The same screens and recipe as slope_frames: each star samples its own
+    grid's edge midpoints and corners; sigma[g] = noise_frac * rms of star g's
+    noiseless slopes over frames 0..3; the noise of frame f is drawn from the
+    same stream, star after star.  With one grid for all stars the result is
+    slope_frames' valid slopes, number for number.
+    """
+    D, eps, n_gs = cfg["D"], cfg["obstruction"], len(cfg["gs"])
+    gs_n = [int(x) for x in cfg.get("gs_n", [cfg["n"]] * n_gs)]
+    grids = {n: _grids(cfg, n) for n in set(gs_n)}
+
+    def clean(f):
+        scr = _screens(cfg, seed, f, screen_px)
+        return [_sample(cfg, scr, grids[gs_n[g]], stars=[g])[0] for g in range(n_gs)]
+
+    calib = [clean(f) for f in range(N_CALIBRATION_FRAMES)]
+    sigma = np.array([cfg["noise_frac"] * np.sqrt(np.mean([c[g] ** 2 for c in calib])) for g in range(n_gs)])
+    masks = [_subaperture_mask(gs_n[g], eps) for g in range(n_gs)]
+    out = []
+    for f in range(n_frames):
+        sl = calib[f] if f < N_CALIBRATION_FRAMES else clean(f)
+        rng = _rng(seed, f, 999)
+        vec = []
+        for g in range(n_gs):
+            noisy = sl[g] + sigma[g] * rng.standard_normal((2, gs_n[g], gs_n[g]))
+            vec += [noisy[0][masks[g]], noisy[1][masks[g]]]
+        out.append(np.concatenate(vec))
+    return np.array(out), sigma
+
+
+def _subaperture_mask(n, obstruction):
+    """Valid subapertures: centre inside the annular pupil (row-major order)."""
+    j = np.arange(n)
+    q = (2 * j[None, :] + 1 - n) ** 2 + (2 * j[:, None] + 1 - n) ** 2
+    return (q <= n * n) & (q >= (obstruction * n) ** 2)
 
 
 def wind(cfg):

@@ -66,3 +66,26 @@ def test_elongated_noise_model():
     Cn = W.elongated_noise(ngs, 0.1, k=3.0)
     assert np.array_equal(Cn[..., 0], np.full(Cn.shape[:3], 0.1 ** 2))
     assert np.array_equal(Cn[..., 2], np.zeros(Cn.shape[:3]))
+
+
+def test_mixed_grid_frames():
+    # guide stars on grids of their own (natural stars on a coarse grid): with
+    # one grid for all stars the generator reproduces slope_frames' valid
+    # slopes number for number; with mixed grids each star has its own valid
+    # count, and its noise level follows its own slopes
+    from paper_1806_07938_gb300 import workloads as W
+    from oracle import geometry as geo
+    cfg = dict(name="mix", D=4.0, obstruction=0.2, n=12, r0=0.15, L0=25.0, layers=[(0.0, 0.6), (8e3, 0.4)],
+               gs=W.ring(2, 20 * W.ARCSEC, 90e3) + W.ring(1, 30 * W.ARCSEC, 0.0), targets=[(0.0, 0.0)],
+               noise_frac=0.05)
+    full, sig = W.slope_frames(cfg, 6, seed=5, screen_px=128)
+    mask = geo.subaperture_mask(12, 0.2)
+    vec, sig2 = W.slope_frames_mixed(dict(cfg, gs_n=[12, 12, 12]), 6, seed=5, screen_px=128)
+    assert np.array_equal(vec, full[..., mask].reshape(6, -1))
+    assert np.array_equal(sig, sig2)
+    mixed, sig3 = W.slope_frames_mixed(dict(cfg, gs_n=[12, 12, 4]), 6, seed=5, screen_px=128)
+    nf, nc = int(mask.sum()), int(geo.subaperture_mask(4, 0.2).sum())
+    assert mixed.shape == (6, 2 * 2 * nf + 2 * nc)
+    assert np.array_equal(mixed[:, :4 * nf], vec[:, :4 * nf])        # the laser stars are unchanged
+    assert np.array_equal(sig3[:2], sig[:2]) and sig3[2] != sig[2]
+    assert np.all(np.isfinite(mixed))
