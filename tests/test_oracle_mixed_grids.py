@@ -156,3 +156,31 @@ def test_cross_block_matches_simulated_screens():
     print(good, good_x, bad_x)
     assert good < 2.5 and good_x < 2.5
     assert bad_x > 4 * good_x
+
+
+@pytest.mark.parametrize("H", [0.0, 90e3])
+def test_coarse_projection_columns_are_sums_of_fine_columns(H):
+    # the same telescoping on the projection side: each coarse slope's column
+    # of Sigma_phi_s (Eq. covIterative2) is the sum of the three fine columns
+    # along its centre line, for every target phase point
+    base = small_cfg(n=12, n_gs=1, lgs=H > 0, D=4.0, obstruction=0.0, targets=((5e-5, -2e-5),))
+    g = tuple(base["gs"][0])
+    cfg = dict(base, gs=[g, g], gs_n=[12, 4], noise_sigma=[0.1, 0.1])
+    F = cov.cos_exact(cfg, 0)
+    fine = geo.subaperture_mask(12, 0.0)
+    coarse = geo.subaperture_mask(4, 0.0)
+    fidx = -np.ones((12, 12), dtype=np.int64)
+    fidx[fine] = np.arange(fine.sum())
+    nvf, nvc = int(fine.sum()), int(coarse.sum())
+    scale = np.abs(F).max()
+    checked = 0
+    for e, (i, j) in enumerate(geo.valid_list(coarse)):
+        for comp in (0, 1):
+            cells = [(3 * i + 1, 3 * j + k) for k in range(3)] if comp == 0 else \
+                [(3 * i + k, 3 * j + 1) for k in range(3)]
+            if any(not fine[c] for c in cells):
+                continue
+            want = sum(F[:, comp * nvf + fidx[c]] for c in cells)
+            assert np.abs(F[:, 2 * nvf + comp * nvc + e] - want).max() <= 1e-12 * scale
+            checked += 1
+    assert checked >= 16
